@@ -1,0 +1,329 @@
+"""Benchmark: LJ MD particle-steps/s on one GB300 (and N independent replicas).
+
+Workload (the large monatomic LJ fluid): fcc 100^3 x 4 = 4,000,000 particles,
+density 0.8442, T = 0.722, truncated-shifted LJ eps = sigma = 1, rc = 2.5,
+skin 0.3, dt = 0.005, NVE velocity-Verlet with energies every step.  A bench
+"step" is one MD step: integrate, list update by the skin rule (amortised),
+force, finalize, energy reductions.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+(the reference arm of this method; there is no runnable code in the paper).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "LJ MD particle-steps/s (N=4.0M fcc LJ fluid, FP32 forces + double-single integration)"
+UNIT = "particle-steps/s"
+WORKLOAD = {"workload": "LJ fluid fcc 100^3 x 4 = 4,000,000 particles, rho 0.8442, T 0.722, "
+                        "rc 2.5, skin 0.3, dt 0.005, NVE",
+            "n_particles": 4000000, "dt": 0.005, "skin": 0.3, "rcut": 2.5,
+            "thermo": "every step",
+            "l2": "inputs larger than L2 (~2.8 GB working set vs 129 MB L2)"}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                   "-lms", "200"]
+            if self.gpu_id is not None:
+                cmd += ["-i", str(self.gpu_id)]
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _gpu_smi_id(dev):
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return None
+
+
+# ----------------------------------------------------------------------------
+# oracle (CPU) timing
+# ----------------------------------------------------------------------------
+def oracle_sample(nsteps, budget_s=None, ncell=None):
+    """Time the FP64 oracle on an fcc sample of the workload (same density,
+    temperature and parameters); returns (particle-steps/s, n, steps, secs)."""
+    import oracle
+    from paper_2406_04210_gb300 import inputs
+    if ncell is None:
+        # ~6 us per particle-step for a short run incl. the initial list build
+        n_target = max(4000, min(4_000_000, budget_s / (6e-6 * max(nsteps, 1))))
+        ncell = max(10, int((n_target / 4) ** (1 / 3)))
+    s = inputs.fcc_system(ncell, seed=inputs.SEEDS["lj4m"])
+    lj = oracle.LJ(s.eps, s.sigma, s.rcut)
+    t0 = time.perf_counter()
+    oracle.run(s.box, s.pos, s.vel, lj, s.skin, s.dt, nsteps)
+    dt = time.perf_counter() - t0
+    return s.n * nsteps / dt, s.n, nsteps, dt
+
+
+def run_reference(args):
+    """The reference arm: the FP64 oracle on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    # warm-up and timed steps on one sample sized to finish in ~2-3 minutes
+    total = args.steps + args.warmup
+    n_target = max(4000, min(4_000_000, 150.0 / (6e-6 * max(total, 1))))
+    ncell = max(10, int((n_target / 4) ** (1 / 3)))
+    import oracle
+    from paper_2406_04210_gb300 import inputs
+    s = inputs.fcc_system(ncell, seed=inputs.SEEDS["lj4m"])
+    lj = oracle.LJ(s.eps, s.sigma, s.rcut)
+    w = oracle.run(s.box, s.pos, s.vel, lj, s.skin, s.dt, max(args.warmup, 0))
+    t0 = time.perf_counter()
+    oracle.run(s.box, w["pos"], w["vel"], lj, s.skin, s.dt, args.steps)
+    sec = time.perf_counter() - t0
+    value = s.n * args.steps / sec
+    sample = (f"fcc {ncell}^3 x 4 = {s.n} particles of the workload's fluid, {args.steps} "
+              f"velocity-Verlet steps after {args.warmup} warm-up steps, single thread")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": dict(WORKLOAD),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+def timed_integrate(box, dt, steps, thermo_dev):
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    box.integrate(dt, steps, thermo=True, out=thermo_dev)
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def run_gpu(args):
+    import torch
+    from paper_2406_04210_gb300 import build, inputs, ljmd
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0 or world == 1:
+        build.build()
+    if dist:
+        dist.barrier()
+    ljmd.load()
+
+    # independent replica per rank (replicas only: the path does not shard)
+    s = inputs.fcc_system(100, seed=inputs.SEEDS["lj4m"] + rank)
+    n = s.n
+    box = ljmd.from_system(s, "mixed_ds")
+    thermo = torch.zeros((max(args.steps, args.warmup, 1), 1, 4), dtype=torch.float64,
+                         device="cuda")
+    if args.warmup:
+        box.integrate(s.dt, args.warmup, thermo=True, out=thermo[: args.warmup])
+    box.set_profiling(True)
+    info0 = box.info()
+    sampler = ClockSampler(_gpu_smi_id(local))
+    if dist:
+        dist.barrier()
+    sampler.start()
+    ms = timed_integrate(box, s.dt, args.steps, thermo[: args.steps])
+    clocks = sampler.stop()
+    info1 = box.info()
+    prof = box.profile()
+    launches = int(info1.launches - info0.launches)
+    th = thermo[: args.steps].cpu().numpy()
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = n * world * args.steps / (ms / 1e3)
+
+    # roofline of the dominant kernel (pair force), timed in the graph
+    f_ms, f_n = prof["force"]
+    f_avg = f_ms / max(f_n, 1)
+    list_entries = info1.list_entries
+    force_bytes = 4 * list_entries + 36 * n      # list + count + own posq + force out
+    peak, peak_kind = _peaks()
+    achieved = force_bytes / (f_avg / 1e3) / 1e9
+    total_prof = sum(v[0] for v in prof.values())
+    phases = {k: {"ms_per_step": v[0] / max(args.steps, 1),
+                  "share": v[0] / total_prof if total_prof else None} for k, v in prof.items()}
+    E = th[:, 0, 0] + th[:, 0, 1]
+    box.set_profiling(False)
+
+    # end to end through the C ABI with host buffers: state in, K steps,
+    # energies and state out
+    pos_h = torch.from_numpy(s.pos).pin_memory()
+    vel_h = torch.from_numpy(s.vel).pin_memory()
+    pos_o = torch.empty_like(pos_h).pin_memory()
+    vel_o = torch.empty_like(vel_h).pin_memory()
+    img_o = torch.empty((n, 3), dtype=torch.int32).pin_memory()
+    th_h = torch.empty((args.steps, 1, 4), dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    box.set_state(pos_h.numpy(), vel_h.numpy())
+    box.integrate(s.dt, args.steps, thermo=True, out=th_h.numpy())
+    box._check(box._lib.md_get_state(box._h, pos_o.data_ptr(), vel_o.data_ptr(),
+                                     img_o.data_ptr()), "md_get_state")
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": n * args.steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(48 * n / max(args.steps, 1)),
+           "d2h_bytes_per_step": int((60 * n) / max(args.steps, 1) + 32),
+           "what": "md_set_state(host x, v) + md_integrate(K steps, host energies) + "
+                   "md_get_state(host x, v, images), wall clock"}
+    box.close()
+    del box
+
+    # other precisions on the same workload
+    prec = {"mixed_ds": value / world}
+    for p, k in (("mixed_fp64", args.steps), ("fp64", max(20, args.steps // 10))):
+        b2 = ljmd.from_system(s, p)
+        b2.integrate(s.dt, min(args.warmup, 10) or 1, thermo=True, out=thermo[:10])
+        ms2 = timed_integrate(b2, s.dt, k, thermo[:k])
+        prec[p] = n * k / (ms2 / 1e3)
+        b2.close()
+
+    if rank != 0:
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    cpu = None
+    if world == 1:
+        ps, ns, st, sec = oracle_sample(10, ncell=40)
+        cpu = {"value": ps, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"fcc 40^3 x 4 = {ns} particles of the workload's fluid, {st} "
+                         f"velocity-Verlet steps incl. the initial list build, "
+                         f"{sec:.1f} s on one host core"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / max(args.steps, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 forces / double-single state",
+        "data": "synthetic", "config": dict(WORKLOAD, parallelism=f"replicas{world}"),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": TRAFFIC_PER_LAUNCH,
+                     "kernel": "k_force_f32 (pair force, energy+virial)",
+                     "bytes_per_launch": force_bytes, "avg_launch_ms": f_avg,
+                     "peak_kind": f"hbm_gbs of {peak_kind} peaks (copy, burst)"},
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+        "phases": phases, "precisions": prec,
+        "energy": {"E_per_particle_first": float(E[0] / n), "E_per_particle_last": float(E[-1] / n),
+                   "drift_per_particle": float((E[-1] - E[0]) / n)},
+        "rebuilds_in_timed_region": int(info1.rebuilds - info0.rebuilds),
+        "adjoint_forward_ratio": None,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+#: dram read+write bytes per force launch from the committed ncu summary of
+#: the current kernel (profiles/k_force_f32_lj4m.md); None when not measured
+TRAFFIC_PER_LAUNCH = None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=100)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

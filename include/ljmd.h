@@ -1,0 +1,216 @@
+/*
+ * ljmd.h -- C ABI of the GB300 truncated Lennard-Jones MD library (libljmd.so).
+ *
+ * The library advances N particles in a periodic orthorhombic box under
+ * truncated(-shifted) Lennard-Jones pair forces with the velocity-Verlet
+ * integrator, using Verlet neighbour lists built by particle binning -- the
+ * MD hot path of arXiv 2406.04210 (Sec. 3, Code structure: modules for
+ * forces and integrators, `integrate`/`finalize` half steps around the
+ * `force` evaluation, Verlet lists from a spatial decomposition; Sec. 4:
+ * Lennard-Jones pair forces with velocity-Verlet; Sec. 5, Truncated Force
+ * Performance Study: truncated pair forces over Verlet lists, whose force and
+ * list-update kernels dominate the run time).  The paper gives the problem,
+ * not formulas; the textbook forms used are:
+ *
+ *   U_ab(r) = 4 eps_ab [(sigma_ab/r)^12 - (sigma_ab/r)^6] - shift_ab, r < rc_ab
+ *   F_i = sum_{j != i, r_ij < rc} 48 eps/r^2 [(sigma/r)^12 - (sigma/r)^6/2] d_ij,
+ *         d_ij = minimum image of x_i - x_j
+ *   integrate: v += dt/2 F; x += dt v     (unit mass)
+ *   finalize:  v += dt/2 F
+ *   E_pot = sum_{i<j} U, W = sum_{i<j} d_ij . F_ij, E_kin = 1/2 sum v^2,
+ *   T = 2 E_kin / (3N - 3)
+ *
+ * Conventions shared by every entry point
+ *  - Array arguments are plain pointers that may point to host memory or to
+ *    device memory of the machine's GPU; the library detects which
+ *    (cudaPointerGetAttributes) and copies as needed.  Particle arrays are in
+ *    USER order (the order given at creation), n x 3 row-major (AoS) FP64
+ *    unless stated.  The library never keeps a caller pointer after a call
+ *    returns.
+ *  - Calls are ordered after work already queued on the `stream` given at
+ *    creation, and work queued on that stream afterwards is ordered after the
+ *    call.  Calls return once their results are in the caller's buffers
+ *    (every call synchronises the box's internal stream before returning).
+ *  - Errors are returned as md_status; nothing is thrown across the ABI.  A
+ *    message for the last failing call of a box is in md_last_error().
+ *  - A box (md_box) owns all of its device memory.  Memory comes from the
+ *    allocator installed with md_set_allocator (default: cudaMalloc/cudaFree).
+ *  - A batch holds nrep independent replicas (boxes of their own, each with
+ *    its own particle count and edge lengths, sharing the LJ parameters); a
+ *    single box is a batch with nrep = 1.  Batched arrays concatenate the
+ *    replicas in order.
+ */
+#ifndef LJMD_H
+#define LJMD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct md_box md_box;
+
+typedef enum {
+    MD_OK = 0,
+    MD_ERR_ARG = 1,            /* invalid argument or call order                */
+    MD_ERR_CUDA = 2,           /* a CUDA runtime call failed                    */
+    MD_ERR_OOM = 3,            /* the allocator returned NULL                   */
+    MD_ERR_CAPACITY = 4,       /* neighbour-list capacity exceeded (the library
+                                  regrows and retries internally; returned only
+                                  if the regrow itself fails)                   */
+    MD_ERR_BOX_TOO_SMALL = 5,  /* rc_max + skin >= half a box edge             */
+    MD_ERR_NONFINITE = 6,      /* a non-finite force or position was produced   */
+    MD_ERR_TIMEOUT = 7,        /* a bounded device-side wait gave up            */
+    MD_ERR_STATE = 8           /* no matching forward record (md_adjoint)       */
+} md_status;
+
+/* Arithmetic of a box (Sec. 3, Code structure: modules carry a floating-point
+ * type "single, mixed precision, double"; the mixed form is HAL's MD
+ * double-single accumulation). */
+typedef enum {
+    MD_PREC_MIXED_DS = 0,   /* FP32 pair forces from cell-relative offsets,
+                               double-single (2 x FP32) positions/velocities   */
+    MD_PREC_MIXED_FP64 = 1, /* FP32 pair forces, FP64 positions/velocities     */
+    MD_PREC_FP64 = 2        /* FP64 pair forces and FP64 integration           */
+} md_precision;
+
+/* Device allocator hook: alloc(bytes, ctx) returns a device pointer of the
+ * current device aligned to 256 bytes, or NULL; free(ptr, ctx) releases it.
+ * Installed process-wide; boxes created afterwards use it for every device
+ * allocation they make (at creation, md_set_lj and list regrowth).  Passing
+ * NULL functions restores cudaMalloc/cudaFree.  Not thread-safe against
+ * concurrent box creation. */
+typedef void* (*md_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*md_free_fn)(void* ptr, void* ctx);
+md_status md_set_allocator(md_alloc_fn alloc, md_free_fn free_, void* ctx);
+
+/* Create a batch of nrep replicas on the current CUDA device.
+ *   n[nrep]        particle count of each replica (>= 0)
+ *   box[nrep*3]    edge lengths (Lx, Ly, Lz) of each replica (> 0)
+ *   type[sum n]    species id of each particle (0 <= type < ntypes given to
+ *                  md_set_lj), or NULL for all zero
+ *   pos[sum n * 3] positions; any real values (wrapped into [0, L) on entry)
+ *   vel[sum n * 3] velocities, or NULL for zero
+ *   stream         cudaStream_t the calls are ordered with (NULL = legacy)
+ * Host-array arguments n and box must be host memory.  md_set_lj must be
+ * called before any force, update or integrate call. */
+md_status md_batch_create(md_box** out, int32_t nrep, const int64_t* n,
+                          const double* box, const int32_t* type,
+                          const double* pos, const double* vel,
+                          md_precision prec, void* stream);
+
+/* md_batch_create with nrep = 1; box[3] is host memory. */
+md_status md_box_create(md_box** out, int64_t n, const double box[3],
+                        const int32_t* type, const double* pos,
+                        const double* vel, md_precision prec, void* stream);
+
+/* Free all device memory of the box (after its queued work completes). */
+md_status md_box_destroy(md_box* b);
+
+/* Set the truncated LJ pair parameters (host arrays, ntypes x ntypes,
+ * row-major, symmetric; 1 <= ntypes <= 8), the Verlet skin and whether the
+ * energy is shifted to zero at the cutoff.  The list radius is
+ * rl = max(rcut) + skin; cells are floor(L/rl) per dimension.  Returns
+ * MD_ERR_BOX_TOO_SMALL if rl >= L/2 for any replica.  Rebuilds the lists and
+ * recomputes the forces at the current positions. */
+md_status md_set_lj(md_box* b, int32_t ntypes, const double* eps,
+                    const double* sigma, const double* rcut, double skin,
+                    int32_t energy_shift);
+
+/* Neighbour-list update (Sec. 3, Code structure; Sec. 5): re-bin and rebuild
+ * the lists of every replica in which some particle moved more than skin/2
+ * since its last build, or of all replicas if force_rebuild != 0.  *rebuilt
+ * (nullable, host) receives the number of replicas rebuilt. */
+md_status md_neighbour_update(md_box* b, int32_t force_rebuild,
+                              int32_t* rebuilt);
+
+/* Pair forces at the current positions (updating lists first if needed).
+ *   force_out  nullable, (sum n) x 3 FP64, user order
+ *   epot, virial nullable, nrep entries each (E_pot and W per replica) */
+md_status md_force(md_box* b, double* force_out, double* epot, double* virial);
+
+/* Advance nsteps velocity-Verlet steps of size dt (Sec. 3, Fig. 1:
+ * integrate, force, finalize), rebuilding lists by the skin rule.
+ *   ckpt_every  0: plain run.  k > 0: record the run for md_adjoint, storing
+ *               the state every k steps (nsteps must be a multiple of k).
+ *   thermo_out  nullable, nsteps x nrep x 4 FP64: E_pot, E_kin, W, T after
+ *               each step.  When NULL no energies are computed. */
+md_status md_integrate(md_box* b, double dt, int64_t nsteps, int32_t ckpt_every,
+                       double* thermo_out);
+
+/* Reverse-mode derivative of the run recorded by the last md_integrate with
+ * ckpt_every > 0 (its checkpoints are replayed segment by segment).
+ *   lam_x_T, lam_v_T  dL/dx and dL/dv at the end of the run, (sum n) x 3
+ *   lam_x_0, lam_v_0  out: dL/dx_0 and dL/dv_0, (sum n) x 3
+ *   dL_deps, dL_dsigma out (nullable): ntypes x ntypes, symmetric; the entry
+ *                     (a,b) is the derivative with respect to the single
+ *                     symmetric parameter eps_ab (sigma_ab), rcut held fixed.
+ * The paper has no adjoint; this follows from differentiating the steps
+ * above (velocity-Verlet is differentiated exactly, one Hessian-vector
+ * product of U per step).  Returns MD_ERR_STATE if no recorded run exists.
+ * Only MD_PREC_MIXED_DS / MD_PREC_MIXED_FP64 / MD_PREC_FP64 single-replica
+ * and batched boxes are supported alike. */
+md_status md_adjoint(md_box* b, const double* lam_x_T, const double* lam_v_T,
+                     double* lam_x_0, double* lam_v_0, double* dL_deps,
+                     double* dL_dsigma);
+
+/* Current state in user order: pos in [0, L) FP64, vel FP64, image counts
+ * (number of box lengths crossed), each nullable. */
+md_status md_get_state(md_box* b, double* pos, double* vel, int32_t* image);
+
+/* Replace positions (wrapped into [0,L)) and, if vel != NULL, velocities;
+ * image counts are reset to zero; lists are rebuilt and forces recomputed. */
+md_status md_set_state(md_box* b, const double* pos, const double* vel);
+
+/* Neighbour lists as last built, for inspection: count[sum n] (user order)
+ * and, if nbr != NULL, the user indices of each particle's neighbours in
+ * nbr[i*cap ...] (unsorted; entries beyond count are left untouched); pos
+ * (nullable) receives the FP64 positions the lists were built from.  Returns
+ * MD_ERR_CAPACITY if some count exceeds cap (counts are still written). */
+md_status md_get_nlist(md_box* b, int32_t* count, int64_t* nbr, int64_t cap,
+                       double* pos);
+
+typedef struct {
+    int64_t n_total;        /* sum of n over replicas                         */
+    int32_t nrep;
+    int32_t ntypes;
+    int32_t capacity;       /* neighbour-list slots per particle              */
+    int32_t precision;      /* md_precision                                   */
+    int64_t ncell_total;    /* cells over all replicas                        */
+    int64_t rebuilds;       /* list builds so far (summed over replicas)      */
+    int64_t steps;          /* velocity-Verlet steps done                     */
+    int64_t device_bytes;   /* device memory held                             */
+    double rlist;           /* max(rcut) + skin                               */
+    int64_t launches;       /* kernels launched so far (graph nodes included) */
+    int64_t list_entries;   /* sum of list lengths at the last builds          */
+} md_info;
+
+md_status md_get_info(md_box* b, md_info* out);
+
+/* Tuning.  block_force / block_list: reserved (0).  capacity: neighbour-list
+ * slots per particle to lay the lists out with now and at later parameter
+ * changes (0 = automatic: 1.3 x the mean count at the densest replica + 16).
+ * Lists always regrow by themselves when a build needs more slots. */
+md_status md_set_tuning(md_box* b, int32_t block_force, int32_t block_list,
+                        int32_t capacity);
+
+/* Phase timing of md_integrate.  md_set_profiling(b, 1) resets the counters
+ * and makes later md_integrate calls record CUDA events around each phase of
+ * every step on the box's stream (inside the captured graphs); off by
+ * default.  md_get_profile fills ms[4] (accumulated milliseconds) and
+ * launches[4] (phase executions) for the phases 0 = integrate/finalize,
+ * 1 = list update (binning, sort, list build; early exits included),
+ * 2 = pair force, 3 = energy reductions.  Either output may be NULL. */
+md_status md_set_profiling(md_box* b, int32_t on);
+md_status md_get_profile(md_box* b, double* ms, int64_t* launches);
+
+const char* md_last_error(const md_box* b);
+const char* md_status_string(md_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LJMD_H */

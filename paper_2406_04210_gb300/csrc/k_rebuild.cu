@@ -1,0 +1,393 @@
+// k_rebuild.cu -- particle binning, counting sort by cell and Verlet-list build.
+//
+// Sec. 3 (Code structure): Verlet neighbour lists are built efficiently from
+// a spatial decomposition of the particles ("particle binning"); Sec. 5
+// (Truncated Force Performance Study): the list update is ~30 % of the run
+// time.  A rebuild of replica r runs only when rep_needs_rebuild(r) (the skin
+// rule: some particle moved more than skin/2 since the last build, or the
+// host forced it); every kernel here tests that flag per work item, so the
+// whole sequence can sit in a CUDA graph and cost one early exit per kernel
+// when no replica needs it.
+//
+// Sequence: k_bin (new cell of every particle, counts) -> k_scan_tiles +
+// k_scan_add (exclusive scan of the counts per replica) -> k_scatter (slot
+// per particle) -> k_sortgather (order inside each cell by user index, so
+// the layout is a deterministic function of the positions; gather into the
+// sorted arrays) -> k_nlist (27-cell search).
+#include <climits>
+
+#include "ljmd_internal.cuh"
+
+namespace {
+
+constexpr int kScanTile = 4096;   // cells per scan tile
+
+__device__ __forceinline__ int cell_coords(const RepDev& R, int gc, int& cx, int& cy)
+{
+    int local = gc - R.cell_off;
+    cx = local % R.nc[0];
+    int t = local / R.nc[0];
+    cy = t % R.nc[1];
+    return t / R.nc[1];
+}
+
+// 8-byte component c of particle p of an integrator array in the layout of
+// the box precision (FP64: one double; DS: hi/lo floats in two planes).
+__device__ __forceinline__ void copy_acc(const BoxDev& b, double* dst, const double* src, int c,
+                                         int q, int p)
+{
+    if (b.prec == 0) {
+        const float* s = reinterpret_cast<const float*>(src);
+        float* d = reinterpret_cast<float*>(dst);
+        d[c * b.np + q] = s[c * b.np + p];
+        d[3 * b.np + c * b.np + q] = s[3 * b.np + c * b.np + p];
+    } else {
+        dst[c * b.np + q] = src[c * b.np + p];
+    }
+}
+
+__device__ __forceinline__ double load_off(const BoxDev& b, int c, int p)
+{
+    if (b.prec == 0) {
+        const float* s = reinterpret_cast<const float*>(b.off);
+        return (double)s[c * b.np + p] + (double)s[3 * b.np + c * b.np + p];
+    }
+    return b.off[c * b.np + p];
+}
+
+// ---------------------------------------------------------------------------
+// k_bin: wrapped FP64 position of every particle of a rebuilding replica,
+// its new cell, and the old-order copies used by the gather.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(LJ_CHUNK) k_bin(BoxDev b, int from_abs)
+{
+    for (int w = blockIdx.x; w < b.nchunk; w += gridDim.x) {
+        int4 ch = b.chunk[w];
+        int r = ch.x;
+        if (!rep_needs_rebuild(b, r)) continue;
+        int p = ch.y + (int)threadIdx.x;
+        if (p >= ch.z) continue;
+        const RepDev& R = b.rep[r];
+        double x[3];
+        int im[3];
+        if (from_abs) {
+            for (int c = 0; c < 3; ++c) {
+                x[c] = b.xabs[c * b.np + p];
+                im[c] = b.img[c * b.np + p];
+            }
+        } else {
+            int cx, cy;
+            int cz = cell_coords(R, b.cell[p], cx, cy);
+            int cc[3] = {cx, cy, cz};
+            for (int c = 0; c < 3; ++c) {
+                double centre = ((double)cc[c] + 0.5) * R.ell[c];
+                x[c] = centre + load_off(b, c, p);
+                im[c] = b.img[c * b.np + p];
+            }
+        }
+        int q[3];
+        for (int c = 0; c < 3; ++c) {
+            double L = R.L[c];
+            double f = floor(x[c] / L);
+            if (f != 0.0) {
+                x[c] = x[c] - L * f;
+                im[c] += (int)f;
+            }
+            int qc = (int)(x[c] * R.inv_ell[c]);
+            q[c] = qc < 0 ? 0 : (qc >= R.nc[c] ? R.nc[c] - 1 : qc);
+        }
+        int gc = R.cell_off + q[0] + R.nc[0] * (q[1] + R.nc[1] * q[2]);
+        for (int c = 0; c < 3; ++c) {
+            b.xabsB[c * b.np + p] = x[c];
+            b.imgB[c * b.np + p] = im[c];
+            copy_acc(b, b.velB, b.vel, c, p, p);
+        }
+        b.uidB[p] = b.uid[p];
+        b.typeB[p] = b.type[p];
+        b.cellB[p] = gc;
+        atomicAdd(&b.cell_count[gc], 1);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Exclusive scan of cell counts inside each replica, in two passes over
+// tiles of kScanTile cells: k_scan_tiles writes the tile-local prefix into
+// cell_start and the tile total into tile_sum; k_scan_add adds the totals of
+// the replica's earlier tiles plus the replica's first slot.
+// tiles[t] = (rep, first cell, end cell, first tile of the replica).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int block_excl_scan(int v, int* s_warp, int& total)
+{
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int nw = blockDim.x >> 5;
+        int x = lane < nw ? s_warp[lane] : 0;
+        int xi = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(0xffffffffu, xi, o);
+            if (lane >= o) xi += t;
+        }
+        if (lane < nw) s_warp[lane] = xi - x;   // exclusive warp offsets
+        if (lane == nw - 1) s_warp[32] = xi;    // block total
+    }
+    __syncthreads();
+    int r = incl - v + s_warp[warp];
+    total = s_warp[32];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_tiles(BoxDev b, const int4* tiles, int ntiles,
+                                                      int* tile_sum)
+{
+    __shared__ int s_warp[33];
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        int4 tl = tiles[t];
+        if (!rep_needs_rebuild(b, tl.x)) continue;   // block-uniform
+        int carry = 0;
+        for (int base = tl.y; base < tl.z; base += blockDim.x) {
+            int c = base + (int)threadIdx.x;
+            int v = c < tl.z ? b.cell_count[c] : 0;
+            int total;
+            int ex = block_excl_scan(v, s_warp, total);
+            if (c < tl.z) b.cell_start[c] = carry + ex;
+            carry += total;
+        }
+        if (threadIdx.x == 0) tile_sum[t] = carry;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_scan_add(BoxDev b, const int4* tiles, int ntiles,
+                                                   const int* tile_sum)
+{
+    __shared__ int s_off;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        int4 tl = tiles[t];
+        if (!rep_needs_rebuild(b, tl.x)) continue;
+        if (threadIdx.x == 0) {
+            int o = b.rep[tl.x].p_off;
+            for (int u = tl.w; u < t; ++u) o += tile_sum[u];
+            s_off = o;
+        }
+        __syncthreads();
+        int o = s_off;
+        for (int c = tl.y + (int)threadIdx.x; c < tl.z; c += blockDim.x) {
+            int s = b.cell_start[c] + o;
+            b.cell_start[c] = s;
+            b.cell_end[c] = s;     // cursor for k_scatter; ends at start + count
+            b.cell_count[c] = 0;   // ready for the next build
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_scatter: claim a slot inside the particle's new cell.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(LJ_CHUNK) k_scatter(BoxDev b)
+{
+    for (int w = blockIdx.x; w < b.nchunk; w += gridDim.x) {
+        int4 ch = b.chunk[w];
+        if (!rep_needs_rebuild(b, ch.x)) continue;
+        int p = ch.y + (int)threadIdx.x;
+        if (p >= ch.z) continue;
+        int slot = atomicAdd(&b.cell_end[b.cellB[p]], 1);
+        b.perm[slot] = p;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_sortgather: one warp per cell.  Rank every member of the cell by user
+// index (count of smaller keys; keys are unique), then gather its state into
+// the sorted arrays and derive its cell-relative offset and FP32 copy.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_sortgather(BoxDev b)
+{
+    const int lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    for (int gc = blockIdx.x * wpb + (threadIdx.x >> 5); gc < b.ncell; gc += gridDim.x * wpb) {
+        int r = b.cell_rep[gc];
+        if (!rep_needs_rebuild(b, r)) continue;   // warp-uniform
+        const RepDev& R = b.rep[r];
+        int s0 = b.cell_start[gc];
+        int n = b.cell_end[gc] - s0;
+        int cx, cy;
+        int cz = cell_coords(R, gc, cx, cy);
+        double centre[3] = {((double)cx + 0.5) * R.ell[0], ((double)cy + 0.5) * R.ell[1],
+                            ((double)cz + 0.5) * R.ell[2]};
+        for (int base = 0; base < n; base += 32) {
+            int idx = base + lane;
+            int p = idx < n ? b.perm[s0 + idx] : -1;
+            int key = idx < n ? b.uidB[p] : INT_MAX;
+            int rank = 0;
+            for (int b2 = 0; b2 < n; b2 += 32) {
+                int k2 = (b2 + lane < n) ? b.uidB[b.perm[s0 + b2 + lane]] : INT_MAX;
+#pragma unroll 8
+                for (int t = 0; t < 32; ++t) {
+                    int kt = __shfl_sync(0xffffffffu, k2, t);
+                    rank += (kt < key) ? 1 : 0;
+                }
+            }
+            if (idx < n) {
+                int q = s0 + rank;
+                int ty = b.typeB[p];
+                float of[3];
+                for (int c = 0; c < 3; ++c) {
+                    double x = b.xabsB[c * b.np + p];
+                    b.xabs[c * b.np + q] = x;
+                    double o = x - centre[c];
+                    if (b.prec == 0) {
+                        float h, l;
+                        ds_from_double(o, h, l);
+                        float* ofs = reinterpret_cast<float*>(b.off);
+                        ofs[c * b.np + q] = h;
+                        ofs[3 * b.np + c * b.np + q] = l;
+                        of[c] = h;
+                    } else {
+                        b.off[c * b.np + q] = o;
+                        of[c] = __double2float_rn(o);
+                    }
+                    copy_acc(b, b.vel, b.velB, c, q, p);
+                    b.img[c * b.np + q] = b.imgB[c * b.np + p];
+                }
+                b.uid[q] = key;
+                b.type[q] = ty;
+                b.cell[q] = gc;
+                float4 pq = make_float4(of[0], of[1], of[2], __int_as_float(ty));
+                b.posq[q] = pq;
+                b.ref[q] = pq;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_nlist: Verlet list of every particle of a rebuilding replica (Sec. 3).
+// Membership |d_ij|^2 < rl^2 is decided in FP32 from the cell-relative
+// offsets; pairs within `band` of rl^2 are re-decided in FP64 from the
+// wrapped positions with the minimum image, in the same operation order as
+// the plain definition, so the lists equal the FP64 definition exactly.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool exact_within(const BoxDev& b, const RepDev& R, int p, int j)
+{
+    double dd[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        double d = __dsub_rn(b.xabs[c * b.np + p], b.xabs[c * b.np + j]);
+        double t = rint(__ddiv_rn(d, R.L[c]));
+        dd[c] = __dsub_rn(d, __dmul_rn(R.L[c], t));
+    }
+    double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dd[0], dd[0]), __dmul_rn(dd[1], dd[1])),
+                          __dmul_rn(dd[2], dd[2]));
+    return d2 < b.rl2;
+}
+
+__global__ void __launch_bounds__(LJ_CHUNK) k_nlist(BoxDev b)
+{
+    __shared__ float4 s_shift[27];
+    int cur_r = -1;
+    const float lo2 = b.rl2f - b.band, hi2 = b.rl2f + b.band;
+    for (int w = blockIdx.x; w < b.nchunk; w += gridDim.x) {
+        int4 ch = b.chunk[w];
+        int r = ch.x;
+        if (!rep_needs_rebuild(b, r)) continue;   // block-uniform
+        const RepDev& R = b.rep[r];
+        if (r != cur_r) {
+            __syncthreads();
+            if (threadIdx.x < 27) {
+                int k = threadIdx.x;
+                s_shift[k] = make_float4((float)(k % 3 - 1) * R.ellf[0],
+                                         (float)((k / 3) % 3 - 1) * R.ellf[1],
+                                         (float)(k / 9 - 1) * R.ellf[2], 0.f);
+            }
+            __syncthreads();
+            cur_r = r;
+        }
+        if (threadIdx.x == 0 && ch.y == R.p_off) atomicAdd(&b.nbuild[r], 1ull);
+        int p = ch.y + (int)threadIdx.x;
+        if (p >= ch.z) continue;
+        float4 pi = b.posq[p];
+        int cx, cy;
+        int cz = cell_coords(R, b.cell[p], cx, cy);
+        uint32_t* out = b.nbr + (size_t)(p >> 5) * (size_t)b.K * 32 + (p & 31);
+        int cnt = 0;
+        for (int k = 0; k < 27; ++k) {
+            int dx = k % 3 - 1, dy = (k / 3) % 3 - 1, dz = k / 9 - 1;
+            int nx = cx + dx, ny = cy + dy, nz = cz + dz;
+            nx = nx < 0 ? nx + R.nc[0] : (nx >= R.nc[0] ? nx - R.nc[0] : nx);
+            ny = ny < 0 ? ny + R.nc[1] : (ny >= R.nc[1] ? ny - R.nc[1] : ny);
+            nz = nz < 0 ? nz + R.nc[2] : (nz >= R.nc[2] ? nz - R.nc[2] : nz);
+            int cn = R.cell_off + nx + R.nc[0] * (ny + R.nc[1] * nz);
+            int js = b.cell_start[cn], je = b.cell_end[cn];
+            float4 sh = s_shift[k];
+            for (int j = js; j < je; ++j) {
+                if (j == p && k == 13) continue;
+                float4 pj = b.posq[j];
+                float ddx = (pi.x - pj.x) - sh.x;
+                float ddy = (pi.y - pj.y) - sh.y;
+                float ddz = (pi.z - pj.z) - sh.z;
+                float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                bool in;
+                if (r2 < lo2) in = true;
+                else if (r2 >= hi2) in = false;
+                else in = exact_within(b, R, p, j);
+                if (in) {
+                    if (cnt < b.K) out[(size_t)cnt * 32] = ((uint32_t)k << LJ_IDX_BITS) | (uint32_t)j;
+                    ++cnt;
+                }
+            }
+        }
+        b.nbr_count[p] = cnt;
+        if (cnt > b.K) {
+            atomicOr(&b.err[0], LJ_ERRBIT_CAPACITY);
+            atomicMax(&b.err[1], cnt);
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_bin(const BoxDev& b, int from_abs, Launch l)
+{
+    k_bin<<<l.grid, LJ_CHUNK, 0, l.s>>>(b, from_abs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan_tiles(const BoxDev& b, const int4* tiles, int ntiles, int* tile_sum,
+                              Launch l)
+{
+    k_scan_tiles<<<l.grid, 1024, 0, l.s>>>(b, tiles, ntiles, tile_sum);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_scan_add<<<l.grid, 256, 0, l.s>>>(b, tiles, ntiles, tile_sum);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(const BoxDev& b, Launch l)
+{
+    k_scatter<<<l.grid, LJ_CHUNK, 0, l.s>>>(b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sortgather(const BoxDev& b, Launch l)
+{
+    k_sortgather<<<l.grid, 256, 0, l.s>>>(b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nlist(const BoxDev& b, Launch l)
+{
+    k_nlist<<<l.grid, LJ_CHUNK, 0, l.s>>>(b);
+    return cudaGetLastError();
+}
+
+int ljmd_scan_tile_cells() { return kScanTile; }

@@ -1,0 +1,1025 @@
+// ljmd_api.cu -- host side of the C ABI declared in include/ljmd.h.
+//
+// Owns the device memory of a box (through the installed allocator hook),
+// orders its work on an internal stream fenced against the caller's stream,
+// and replays the velocity-Verlet step loop from captured CUDA graphs.  Each
+// graph holds `chunk` steps; between graphs the host reads the device error
+// word once, so a neighbour-list overflow found inside a graph is repaired by
+// restoring the state saved before that graph, regrowing the list and
+// replaying it.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ljmd.h"
+#include "ljmd_internal.cuh"
+
+namespace {
+
+md_alloc_fn g_alloc = nullptr;
+md_free_fn g_free = nullptr;
+void* g_ctx = nullptr;
+
+struct Alloc {
+    void* p;
+    size_t bytes;
+};
+
+struct GraphEnt {
+    int64_t nsteps;
+    double dt;
+    int energy;
+    cudaGraphExec_t exec;
+    int64_t kernels;                 // kernel nodes per replay
+    std::vector<cudaEvent_t> ev;     // phase events (profiling), 8 per step
+    std::vector<char> used;          // which (step, phase) pairs were recorded
+};
+
+bool is_device_ptr(const void* p)
+{
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int round_up(int64_t x, int64_t m) { return (int)(((x + m - 1) / m) * m); }
+
+}  // namespace
+
+struct md_box {
+    int device = 0;
+    int nsm = 152;
+    cudaStream_t ustream = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev = nullptr;
+    md_alloc_fn alloc = nullptr;
+    md_free_fn free_ = nullptr;
+    void* actx = nullptr;
+    int prec = 0;
+    int nrep = 0;
+    int64_t ntot = 0;
+    int np = 0;
+    std::vector<RepDev> reps;
+    std::vector<int4> chunks;
+    std::vector<int4> tiles;
+    // LJ
+    bool lj_set = false;
+    int nt = 1;
+    double skin = 0.0, rl = 0.0;
+    bool fresh_abs = true;     // xabs holds the current positions (slot order)
+    bool binned = false;       // cell ids and offsets are valid
+    // device
+    BoxDev d{};
+    RepDev* d_rep = nullptr;
+    int4* d_chunk = nullptr;
+    LJDev* d_lj = nullptr;
+    int4* d_tiles = nullptr;
+    int* d_tile_sum = nullptr;
+    int* d_type_user = nullptr;
+    double* d_thermo = nullptr;
+    int64_t thermo_cap = 0;    // doubles
+    void* d_stage = nullptr;
+    size_t stage_bytes = 0;
+    std::vector<Alloc> allocs;
+    // snapshot of the step-loop state (list overflow repair)
+    std::vector<std::pair<void*, size_t>> snap_src;
+    void* d_snap = nullptr;
+    size_t snap_bytes = 0;
+    // graphs
+    std::vector<GraphEnt> graphs;
+    int64_t chunk_steps = 100;
+    // tuning
+    int min_capacity = 0;
+    int64_t steps = 0;
+    int64_t launches = 0;
+    bool profiling = false;
+    double prof_ms[4] = {0, 0, 0, 0};
+    int64_t prof_n[4] = {0, 0, 0, 0};
+    std::string err;
+};
+
+namespace {
+
+md_status fail(md_box* b, md_status s, const std::string& msg)
+{
+    if (b) b->err = msg;
+    return s;
+}
+
+md_status cuda_fail(md_box* b, cudaError_t e, const char* what)
+{
+    char buf[256];
+    snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
+    return fail(b, MD_ERR_CUDA, buf);
+}
+
+#define CK(b, x)                                               \
+    do {                                                       \
+        cudaError_t e_ = (x);                                  \
+        if (e_ != cudaSuccess) return cuda_fail((b), e_, #x);  \
+    } while (0)
+
+#define CKS(x)                                  \
+    do {                                        \
+        md_status s_ = (x);                     \
+        if (s_ != MD_OK) return s_;             \
+    } while (0)
+
+void* raw_alloc(md_box* b, size_t bytes)
+{
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (bytes == 0) bytes = 256;
+    void* p = nullptr;
+    if (b->alloc) {
+        p = b->alloc(bytes, b->actx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    return p;
+}
+
+void raw_free(md_box* b, void* p)
+{
+    if (!p) return;
+    if (b->free_) b->free_(p, b->actx);
+    else cudaFree(p);
+}
+
+template <class T>
+md_status dev_alloc(md_box* b, T** out, size_t count, bool zero = true)
+{
+    size_t bytes = sizeof(T) * (count ? count : 1);
+    void* p = raw_alloc(b, bytes);
+    if (!p) return fail(b, MD_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+    b->allocs.push_back({p, bytes});
+    if (zero) CK(b, cudaMemsetAsync(p, 0, bytes, b->stream));
+    *out = static_cast<T*>(p);
+    return MD_OK;
+}
+
+void dev_release(md_box* b, void* p)
+{
+    if (!p) return;
+    cudaStreamSynchronize(b->stream);   // no queued work may still use it
+    for (size_t i = 0; i < b->allocs.size(); ++i)
+        if (b->allocs[i].p == p) {
+            raw_free(b, p);
+            b->allocs.erase(b->allocs.begin() + (long)i);
+            return;
+        }
+}
+
+md_status ensure_stage(md_box* b, size_t bytes)
+{
+    if (b->stage_bytes >= bytes) return MD_OK;
+    dev_release(b, b->d_stage);
+    b->d_stage = nullptr;
+    b->stage_bytes = 0;
+    char* p;
+    CKS(dev_alloc(b, &p, bytes, false));
+    b->d_stage = p;
+    b->stage_bytes = bytes;
+    return MD_OK;
+}
+
+void invalidate_graphs(md_box* b)
+{
+    for (auto& g : b->graphs) {
+        cudaGraphExecDestroy(g.exec);
+        for (auto e : g.ev) cudaEventDestroy(e);
+    }
+    b->graphs.clear();
+}
+
+Launch lch(md_box* b) { return Launch{std::max(1, std::min((int)b->d.nchunk, b->nsm * 12)), LJ_CHUNK, b->stream}; }
+Launch lcell(md_box* b) { return Launch{std::max(1, std::min((b->d.ncell + 7) / 8, b->nsm * 8)), 256, b->stream}; }
+
+// Fence: internal stream waits for the caller's stream.
+md_status enter(md_box* b)
+{
+    CK(b, cudaSetDevice(b->device));
+    CK(b, cudaEventRecord(b->ev, b->ustream));
+    CK(b, cudaStreamWaitEvent(b->stream, b->ev, 0));
+    return MD_OK;
+}
+
+// Finish: wait for the box's work; the caller's stream is ordered after it.
+md_status leave(md_box* b)
+{
+    CK(b, cudaEventRecord(b->ev, b->stream));
+    CK(b, cudaStreamWaitEvent(b->ustream, b->ev, 0));
+    CK(b, cudaStreamSynchronize(b->stream));
+    return MD_OK;
+}
+
+// Copy n bytes of input into device memory: returns a device pointer.
+md_status input_ptr(md_box* b, const void* src, size_t bytes, const void** dev, size_t stage_off)
+{
+    if (!src) {
+        *dev = nullptr;
+        return MD_OK;
+    }
+    if (is_device_ptr(src)) {
+        *dev = src;
+        return MD_OK;
+    }
+    CKS(ensure_stage(b, stage_off + bytes));
+    char* dst = static_cast<char*>(b->d_stage) + stage_off;
+    CK(b, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, b->stream));
+    *dev = dst;
+    return MD_OK;
+}
+
+md_status read_err(md_box* b, int* err2)
+{
+    CK(b, cudaMemcpyAsync(err2, b->d.err, 2 * sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+    CK(b, cudaStreamSynchronize(b->stream));
+    return MD_OK;
+}
+
+md_status clear_err(md_box* b)
+{
+    CK(b, cudaMemsetAsync(b->d.err, 0, 2 * sizeof(int), b->stream));
+    return MD_OK;
+}
+
+// ------------------------------------------------------------------------
+// Rebuild / force sequences
+// ------------------------------------------------------------------------
+md_status enqueue_rebuild(md_box* b, int from_abs)
+{
+    Launch l = lch(b);
+    CK(b, launch_bin(b->d, from_abs, l));
+    Launch lt{std::max(1, std::min((int)b->tiles.size(), b->nsm * 2)), 1024, b->stream};
+    CK(b, launch_scan_tiles(b->d, b->d_tiles, (int)b->tiles.size(), b->d_tile_sum, lt));
+    CK(b, launch_scatter(b->d, l));
+    CK(b, launch_sortgather(b->d, lcell(b)));
+    CK(b, launch_nlist(b->d, l));
+    b->launches += 6;
+    return MD_OK;
+}
+
+md_status enqueue_force(md_box* b, int energy, double* thermo_out_dev)
+{
+    CK(b, launch_force(b->d, energy, lch(b)));
+    b->launches += 1;
+    if (energy && thermo_out_dev) {
+        Launch lt{std::max(1, std::min((b->nrep + 3) / 4, b->nsm)), 128, b->stream};
+        CK(b, launch_thermo(b->d, thermo_out_dev, 0, lt));
+        b->launches += 1;
+    }
+    return MD_OK;
+}
+
+md_status set_all_rebuild(md_box* b)
+{
+    std::vector<int> ones(b->nrep, 1);
+    CK(b, cudaMemcpyAsync(b->d.rebuild_req, ones.data(), sizeof(int) * b->nrep,
+                          cudaMemcpyHostToDevice, b->stream));
+    CK(b, cudaStreamSynchronize(b->stream));   // `ones` is pageable and local
+    return MD_OK;
+}
+
+md_status alloc_lists(md_box* b, int K)
+{
+    if (b->d.nbr) dev_release(b, b->d.nbr);
+    b->d.nbr = nullptr;
+    b->d.K = K;
+    uint32_t* nb;
+    CKS(dev_alloc(b, &nb, (size_t)b->np * (size_t)K, false));
+    b->d.nbr = nb;
+    invalidate_graphs(b);
+    return MD_OK;
+}
+
+// Rebuild all replicas now (forced), regrowing the lists until they fit,
+// then recompute the forces.
+md_status full_rebuild(md_box* b)
+{
+    for (int attempt = 0; attempt < 8; ++attempt) {
+        CKS(clear_err(b));
+        CKS(set_all_rebuild(b));
+        CKS(enqueue_rebuild(b, b->fresh_abs ? 1 : 0));
+        int e2[2];
+        CKS(read_err(b, e2));
+        b->binned = true;
+        if (e2[0] & LJ_ERRBIT_CAPACITY) {
+            // binning and sorting completed (xabs still holds the exact
+            // positions, now in sorted slots); only the lists were cut short
+            int K = round_up((int64_t)(e2[1] * 1.15) + 8, 8);
+            CKS(alloc_lists(b, K));
+            continue;
+        }
+        b->fresh_abs = true;
+        CKS(enqueue_force(b, 0, nullptr));
+        return MD_OK;
+    }
+    return fail(b, MD_ERR_CAPACITY, "neighbour list kept overflowing");
+}
+
+md_status snapshot_setup(md_box* b)
+{
+    int np = b->np;
+    b->snap_src.clear();
+    size_t accb = sizeof(double) * 3 * (size_t)np;
+    b->snap_src.push_back({b->d.off, accb});
+    b->snap_src.push_back({b->d.vel, accb});
+    b->snap_src.push_back({b->d.img, sizeof(int) * 3 * (size_t)np});
+    b->snap_src.push_back({b->d.uid, sizeof(int) * (size_t)np});
+    b->snap_src.push_back({b->d.type, sizeof(int) * (size_t)np});
+    b->snap_src.push_back({b->d.cell, sizeof(int) * (size_t)np});
+    size_t tot = 0;
+    for (auto& s : b->snap_src) tot += (s.second + 255) & ~(size_t)255;
+    if (b->snap_bytes < tot) {
+        dev_release(b, b->d_snap);
+        char* p;
+        CKS(dev_alloc(b, &p, tot, false));
+        b->d_snap = p;
+        b->snap_bytes = tot;
+    }
+    return MD_OK;
+}
+
+md_status snapshot(md_box* b, bool restore)
+{
+    size_t o = 0;
+    for (auto& s : b->snap_src) {
+        char* dst = static_cast<char*>(b->d_snap) + o;
+        if (restore) CK(b, cudaMemcpyAsync(s.first, dst, s.second, cudaMemcpyDeviceToDevice, b->stream));
+        else CK(b, cudaMemcpyAsync(dst, s.first, s.second, cudaMemcpyDeviceToDevice, b->stream));
+        o += (s.second + 255) & ~(size_t)255;
+    }
+    return MD_OK;
+}
+
+// The velocity-Verlet loop for `n` steps (Sec. 3, Fig. 1): integrate,
+// conditional list update, force, finalize (fused with the next integrate).
+// With `ge` set, events bracket every phase of every step (profiling).
+md_status enqueue_steps(md_box* b, int64_t n, double dt, int energy, double* ring, GraphEnt* ge)
+{
+    Launch l = lch(b);
+    Launch lt{std::max(1, std::min((b->nrep + 3) / 4, b->nsm)), 128, b->stream};
+    size_t rs = (size_t)b->nrep * 4;
+    auto mark = [&](int64_t s, int ph, int end) -> cudaError_t {
+        if (!ge) return cudaSuccess;
+        size_t k = (size_t)(s * 4 + ph);
+        ge->used[k] = 1;
+        return cudaEventRecord(ge->ev[2 * k + end], b->stream);
+    };
+    for (int64_t s = 0; s <= n; ++s) {
+        int mode = s == 0 ? LJ_STEP_FIRST : (s == n ? LJ_STEP_LAST : LJ_STEP_MID);
+        CK(b, mark(s, 0, 0));
+        CK(b, launch_integrate(b->d, mode, s == 0 ? 0 : energy, dt, l));
+        CK(b, mark(s, 0, 1));
+        b->launches += 1;
+        if (s > 0 && energy) {
+            CK(b, mark(s, 3, 0));
+            CK(b, launch_thermo(b->d, ring + (s - 1) * rs, 1, lt));
+            CK(b, mark(s, 3, 1));
+            b->launches += 1;
+        }
+        if (s == n) break;
+        CK(b, mark(s, 1, 0));
+        CKS(enqueue_rebuild(b, 0));
+        CK(b, mark(s, 1, 1));
+        CK(b, mark(s, 2, 0));
+        CK(b, launch_force(b->d, energy, l));
+        CK(b, mark(s, 2, 1));
+        b->launches += 1;
+    }
+    return MD_OK;
+}
+
+md_status get_graph(md_box* b, int64_t n, double dt, int energy, cudaGraphExec_t* out)
+{
+    for (auto& g : b->graphs)
+        if (g.nsteps == n && g.dt == dt && g.energy == energy) {
+            *out = g.exec;
+            return MD_OK;
+        }
+    if (b->graphs.size() >= 8) invalidate_graphs(b);
+    GraphEnt ge{n, dt, energy, nullptr, 0, {}, {}};
+    if (b->profiling) {
+        ge.ev.resize((size_t)(n + 1) * 8);
+        ge.used.assign((size_t)(n + 1) * 4, 0);
+        for (auto& e : ge.ev) CK(b, cudaEventCreate(&e));
+    }
+    cudaGraph_t graph;
+    int64_t l0 = b->launches;
+    CK(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    md_status st = enqueue_steps(b, n, dt, energy, b->d_thermo, b->profiling ? &ge : nullptr);
+    cudaError_t ce = cudaStreamEndCapture(b->stream, &graph);
+    ge.kernels = b->launches - l0;
+    b->launches = l0;
+    if (st != MD_OK) return st;
+    if (ce != cudaSuccess) return cuda_fail(b, ce, "cudaStreamEndCapture");
+    ce = cudaGraphInstantiate(&ge.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) return cuda_fail(b, ce, "cudaGraphInstantiate");
+    b->graphs.push_back(ge);
+    *out = ge.exec;
+    return MD_OK;
+}
+
+md_status ensure_thermo(md_box* b, int64_t steps)
+{
+    int64_t need = steps * b->nrep * 4;
+    if (b->thermo_cap >= need) return MD_OK;
+    invalidate_graphs(b);   // graphs hold the ring pointer
+    dev_release(b, b->d_thermo);
+    b->d_thermo = nullptr;
+    CKS(dev_alloc(b, &b->d_thermo, (size_t)need));
+    b->thermo_cap = need;
+    return MD_OK;
+}
+
+void copy_reps_to(md_box* b, BoxDev& d)
+{
+    d.nrep = b->nrep;
+    d.np = b->np;
+    d.nchunk = (int)b->chunks.size();
+    d.prec = b->prec;
+}
+
+}  // namespace
+
+// ==========================================================================
+// C ABI
+// ==========================================================================
+extern "C" {
+
+md_status md_set_allocator(md_alloc_fn alloc, md_free_fn free_, void* ctx)
+{
+    if ((alloc == nullptr) != (free_ == nullptr)) return MD_ERR_ARG;
+    g_alloc = alloc;
+    g_free = free_;
+    g_ctx = ctx;
+    return MD_OK;
+}
+
+const char* md_status_string(md_status s)
+{
+    switch (s) {
+    case MD_OK: return "ok";
+    case MD_ERR_ARG: return "invalid argument";
+    case MD_ERR_CUDA: return "CUDA error";
+    case MD_ERR_OOM: return "out of device memory";
+    case MD_ERR_CAPACITY: return "neighbour list capacity exceeded";
+    case MD_ERR_BOX_TOO_SMALL: return "list radius not below half the box";
+    case MD_ERR_NONFINITE: return "non-finite force or position";
+    case MD_ERR_TIMEOUT: return "device wait timed out";
+    case MD_ERR_STATE: return "no recorded forward run";
+    }
+    return "unknown status";
+}
+
+const char* md_last_error(const md_box* b) { return b ? b->err.c_str() : "null box"; }
+
+md_status md_batch_create(md_box** out, int32_t nrep, const int64_t* n, const double* box,
+                          const int32_t* type, const double* pos, const double* vel,
+                          md_precision prec, void* stream)
+{
+    if (!out || nrep < 1 || !n || !box || (prec < 0 || prec > 2)) return MD_ERR_ARG;
+    *out = nullptr;
+    int64_t ntot = 0, np = 0;
+    for (int r = 0; r < nrep; ++r) {
+        if (n[r] < 0) return MD_ERR_ARG;
+        for (int c = 0; c < 3; ++c)
+            if (!(box[3 * r + c] > 0.0) || !std::isfinite(box[3 * r + c])) return MD_ERR_ARG;
+        ntot += n[r];
+        np += round_up(n[r], 32);
+    }
+    if (ntot > 0 && !pos) return MD_ERR_ARG;
+    if (np >= (int64_t(1) << LJ_IDX_BITS)) return MD_ERR_ARG;
+    md_box* b = new md_box();
+    b->alloc = g_alloc;
+    b->free_ = g_free;
+    b->actx = g_ctx;
+    b->prec = prec;
+    b->nrep = nrep;
+    b->ntot = ntot;
+    b->np = (int)std::max<int64_t>(np, 32);
+    b->ustream = static_cast<cudaStream_t>(stream);
+    cudaGetDevice(&b->device);
+    cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, b->device);
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        delete b;
+        return MD_ERR_CUDA;
+    }
+    // replicas and work items
+    int64_t poff = 0, uoff = 0;
+    for (int r = 0; r < nrep; ++r) {
+        RepDev R{};
+        for (int c = 0; c < 3; ++c) R.L[c] = box[3 * r + c];
+        R.p_off = (int)poff;
+        R.n = (int)n[r];
+        R.u_off = (int)uoff;
+        R.chunk_off = (int)b->chunks.size();
+        for (int64_t p = 0; p < n[r]; p += LJ_CHUNK)
+            b->chunks.push_back(make_int4(r, (int)(poff + p), (int)(poff + std::min<int64_t>(p + LJ_CHUNK, n[r])),
+                                          (int)b->chunks.size()));
+        R.nchunk = (int)b->chunks.size() - R.chunk_off;
+        b->reps.push_back(R);
+        poff += round_up(n[r], 32);
+        uoff += n[r];
+    }
+    md_status st = [&]() -> md_status {
+        BoxDev& d = b->d;
+        copy_reps_to(b, d);
+        size_t np3 = 3 * (size_t)b->np;
+        CKS(dev_alloc(b, &b->d_rep, b->reps.size()));
+        CKS(dev_alloc(b, &b->d_chunk, b->chunks.size()));
+        CKS(dev_alloc(b, &b->d_lj, 1));
+        CK(b, cudaMemcpyAsync(b->d_chunk, b->chunks.data(), sizeof(int4) * b->chunks.size(),
+                              cudaMemcpyHostToDevice, b->stream));
+        d.rep = b->d_rep;
+        d.chunk = b->d_chunk;
+        d.lj = b->d_lj;
+        CKS(dev_alloc(b, &d.posq, b->np));
+        CKS(dev_alloc(b, &d.ref, b->np));
+        CKS(dev_alloc(b, &d.off, np3));
+        CKS(dev_alloc(b, &d.vel, np3));
+        CKS(dev_alloc(b, &d.img, np3));
+        CKS(dev_alloc(b, &d.uid, b->np));
+        CKS(dev_alloc(b, &d.type, b->np));
+        CKS(dev_alloc(b, &d.cell, b->np));
+        CKS(dev_alloc(b, &d.xabs, np3));
+        if (prec == MD_PREC_FP64) CKS(dev_alloc(b, &d.force64, np3));
+        else CKS(dev_alloc(b, &d.force4, b->np));
+        CKS(dev_alloc(b, &d.xabsB, np3));
+        CKS(dev_alloc(b, &d.velB, np3));
+        CKS(dev_alloc(b, &d.imgB, np3));
+        CKS(dev_alloc(b, &d.uidB, b->np));
+        CKS(dev_alloc(b, &d.typeB, b->np));
+        CKS(dev_alloc(b, &d.cellB, b->np));
+        CKS(dev_alloc(b, &d.perm, b->np));
+        CKS(dev_alloc(b, &d.nbr_count, b->np));
+        CKS(dev_alloc(b, &d.disp_max, nrep));
+        CKS(dev_alloc(b, &d.rebuild_req, nrep));
+        CKS(dev_alloc(b, &d.nbuild, nrep));
+        CKS(dev_alloc(b, &d.err, 2));
+        CKS(dev_alloc(b, &d.part_f, 2 * std::max<size_t>(1, b->chunks.size())));
+        CKS(dev_alloc(b, &d.part_k, std::max<size_t>(1, b->chunks.size())));
+        CKS(dev_alloc(b, &b->d_type_user, std::max<int64_t>(1, ntot)));
+        CK(b, cudaMemcpyAsync(b->d_rep, b->reps.data(), sizeof(RepDev) * b->reps.size(),
+                              cudaMemcpyHostToDevice, b->stream));
+        CKS(enter(b));
+        if (ntot > 0) {
+            const void *dpos, *dvel = nullptr, *dtype = nullptr;
+            size_t pb = sizeof(double) * 3 * (size_t)ntot;
+            CKS(ensure_stage(b, 2 * pb + sizeof(int) * (size_t)ntot + 256));
+            CKS(input_ptr(b, pos, pb, &dpos, 0));
+            CKS(input_ptr(b, vel, pb, &dvel, pb));
+            CKS(input_ptr(b, type, sizeof(int) * (size_t)ntot, &dtype, 2 * pb));
+            if (dtype) {
+                CK(b, cudaMemcpyAsync(b->d_type_user, dtype, sizeof(int) * (size_t)ntot,
+                                      cudaMemcpyDeviceToDevice, b->stream));
+            }
+            CK(b, launch_upload(d, static_cast<const double*>(dpos), static_cast<const double*>(dvel),
+                                b->d_type_user, 1, lch(b)));
+        }
+        CKS(snapshot_setup(b));
+        CKS(leave(b));
+        return MD_OK;
+    }();
+    if (st != MD_OK) {
+        md_box_destroy(b);
+        return st;
+    }
+    *out = b;
+    return MD_OK;
+}
+
+md_status md_box_create(md_box** out, int64_t n, const double box[3], const int32_t* type,
+                        const double* pos, const double* vel, md_precision prec, void* stream)
+{
+    return md_batch_create(out, 1, &n, box, type, pos, vel, prec, stream);
+}
+
+md_status md_box_destroy(md_box* b)
+{
+    if (!b) return MD_ERR_ARG;
+    cudaSetDevice(b->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    invalidate_graphs(b);
+    for (auto& a : b->allocs) raw_free(b, a.p);
+    b->allocs.clear();
+    if (b->ev) cudaEventDestroy(b->ev);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+    return MD_OK;
+}
+
+md_status md_set_lj(md_box* b, int32_t ntypes, const double* eps, const double* sigma,
+                    const double* rcut, double skin, int32_t energy_shift)
+{
+    if (!b || ntypes < 1 || ntypes > LJ_MAXT || !eps || !sigma || !rcut || !(skin >= 0.0))
+        return fail(b, MD_ERR_ARG, "md_set_lj: bad arguments");
+    int nt = ntypes;
+    double rcmax = 0.0;
+    for (int a = 0; a < nt; ++a)
+        for (int c = 0; c < nt; ++c) {
+            int k = a * nt + c, t = c * nt + a;
+            if (!(eps[k] > 0) || !(sigma[k] > 0) || !(rcut[k] > 0) || eps[k] != eps[t] ||
+                sigma[k] != sigma[t] || rcut[k] != rcut[t])
+                return fail(b, MD_ERR_ARG, "md_set_lj: parameters must be positive and symmetric");
+            rcmax = std::max(rcmax, rcut[k]);
+        }
+    double rl = rcmax + skin;
+    for (int r = 0; r < b->nrep; ++r)
+        for (int c = 0; c < 3; ++c)
+            if (!(rl < 0.5 * b->reps[r].L[c]))
+                return fail(b, MD_ERR_BOX_TOO_SMALL, "md_set_lj: rc + skin >= L/2");
+    CKS(enter(b));
+    // types given at creation must be < ntypes: checked on the host copy
+    if (b->ntot > 0) {
+        std::vector<int> t(b->ntot);
+        CK(b, cudaMemcpyAsync(t.data(), b->d_type_user, sizeof(int) * b->ntot, cudaMemcpyDeviceToHost,
+                              b->stream));
+        CK(b, cudaStreamSynchronize(b->stream));
+        for (int v : t)
+            if (v < 0 || v >= nt) return fail(b, MD_ERR_ARG, "md_set_lj: particle type out of range");
+    }
+    // new cell grid: if it changes while particles are binned, put positions
+    // back into xabs first
+    bool grid_changes = !b->lj_set || rl != b->rl;
+    if (b->lj_set && grid_changes && !b->fresh_abs) {
+        CK(b, launch_materialize(b->d, lch(b)));
+        b->fresh_abs = true;
+    }
+    LJDev h{};
+    h.nt = nt;
+    h.shift_on = energy_shift ? 1 : 0;
+    for (int k = 0; k < nt * nt; ++k) {
+        double s2 = sigma[k] * sigma[k];
+        double rc2 = rcut[k] * rcut[k];
+        double c6 = (s2 / rc2) * (s2 / rc2) * (s2 / rc2);
+        double sh = energy_shift ? 4.0 * eps[k] * (c6 * c6 - c6) : 0.0;
+        h.sig2[k] = (float)s2;
+        h.eps48[k] = (float)(48.0 * eps[k]);
+        h.eps4[k] = (float)(4.0 * eps[k]);
+        h.rc2[k] = (float)rc2;
+        h.shift[k] = (float)sh;
+        h.dsig2[k] = s2;
+        h.deps48[k] = 48.0 * eps[k];
+        h.deps4[k] = 4.0 * eps[k];
+        h.drc2[k] = rc2;
+        h.dshift[k] = sh;
+        h.deps[k] = eps[k];
+        h.dsig[k] = sigma[k];
+    }
+    CK(b, cudaMemcpyAsync(b->d_lj, &h, sizeof h, cudaMemcpyHostToDevice, b->stream));
+    b->nt = nt;
+    b->d.nt = nt;
+    b->skin = skin;
+    b->rl = rl;
+    BoxDev& d = b->d;
+    d.rl2 = rl * rl;
+    d.rl2f = (float)(rl * rl);
+    d.band = (float)(1.5e-4 * rl * rl);
+    double thr = 0.5 * skin - 2e-6;
+    d.disp_thr2 = thr > 0 ? (float)(thr * thr) : 0.0f;
+    if (grid_changes) {
+        invalidate_graphs(b);
+        b->tiles.clear();
+        int cell_off = 0;
+        double maxdens = 0.0;
+        for (int r = 0; r < b->nrep; ++r) {
+            RepDev& R = b->reps[r];
+            for (int c = 0; c < 3; ++c) {
+                R.nc[c] = std::max(1, (int)std::floor(R.L[c] / rl));
+                R.ell[c] = R.L[c] / R.nc[c];
+                R.inv_ell[c] = (double)R.nc[c] / R.L[c];
+                R.ellf[c] = (float)R.ell[c];
+            }
+            R.cell_off = cell_off;
+            R.ncell = R.nc[0] * R.nc[1] * R.nc[2];
+            int first_tile = (int)b->tiles.size();
+            for (int c0 = 0; c0 < R.ncell; c0 += ljmd_scan_tile_cells())
+                b->tiles.push_back(make_int4(r, cell_off + c0,
+                                             cell_off + std::min(R.ncell, c0 + ljmd_scan_tile_cells()),
+                                             first_tile));
+            cell_off += R.ncell;
+            maxdens = std::max(maxdens, R.n / (R.L[0] * R.L[1] * R.L[2]));
+        }
+        d.ncell = cell_off;
+        CK(b, cudaMemcpyAsync(b->d_rep, b->reps.data(), sizeof(RepDev) * b->reps.size(),
+                              cudaMemcpyHostToDevice, b->stream));
+        dev_release(b, d.cell_count);
+        dev_release(b, d.cell_start);
+        dev_release(b, d.cell_end);
+        dev_release(b, (void*)d.cell_rep);
+        dev_release(b, b->d_tiles);
+        dev_release(b, b->d_tile_sum);
+        d.cell_count = d.cell_start = d.cell_end = nullptr;
+        d.cell_rep = nullptr;
+        CKS(dev_alloc(b, &d.cell_count, d.ncell));
+        CKS(dev_alloc(b, &d.cell_start, d.ncell));
+        CKS(dev_alloc(b, &d.cell_end, d.ncell));
+        int* cr;
+        CKS(dev_alloc(b, &cr, d.ncell, false));
+        {
+            std::vector<int> hc(d.ncell);
+            for (int r = 0; r < b->nrep; ++r)
+                for (int c = 0; c < b->reps[r].ncell; ++c) hc[b->reps[r].cell_off + c] = r;
+            CK(b, cudaMemcpyAsync(cr, hc.data(), sizeof(int) * d.ncell, cudaMemcpyHostToDevice, b->stream));
+            CK(b, cudaStreamSynchronize(b->stream));
+        }
+        d.cell_rep = cr;
+        CKS(dev_alloc(b, &b->d_tiles, b->tiles.size(), false));
+        CKS(dev_alloc(b, &b->d_tile_sum, b->tiles.size()));
+        CK(b, cudaMemcpyAsync(b->d_tiles, b->tiles.data(), sizeof(int4) * b->tiles.size(),
+                              cudaMemcpyHostToDevice, b->stream));
+        // list capacity: expected neighbours at the densest replica, +30 %
+        double expect = maxdens * 4.18879020478639 * rl * rl * rl;
+        int K = round_up((int64_t)(1.3 * expect) + 16, 8);
+        if (b->min_capacity > 0) K = b->min_capacity;
+        CKS(alloc_lists(b, K));
+    }
+    b->lj_set = true;
+    CKS(full_rebuild(b));
+    CKS(leave(b));
+    return MD_OK;
+}
+
+md_status md_neighbour_update(md_box* b, int32_t force_rebuild, int32_t* rebuilt)
+{
+    if (!b || !b->lj_set) return fail(b, MD_ERR_ARG, "md_neighbour_update: md_set_lj not called");
+    CKS(enter(b));
+    std::vector<unsigned long long> before(b->nrep), after(b->nrep);
+    CK(b, cudaMemcpyAsync(before.data(), b->d.nbuild, sizeof(unsigned long long) * b->nrep,
+                          cudaMemcpyDeviceToHost, b->stream));
+    CK(b, cudaStreamSynchronize(b->stream));
+    if (force_rebuild) CKS(full_rebuild(b));
+    CK(b, cudaMemcpyAsync(after.data(), b->d.nbuild, sizeof(unsigned long long) * b->nrep,
+                          cudaMemcpyDeviceToHost, b->stream));
+    CKS(leave(b));
+    if (rebuilt) {
+        int k = 0;
+        for (int r = 0; r < b->nrep; ++r) k += after[r] != before[r];
+        *rebuilt = k;
+    }
+    return MD_OK;
+}
+
+md_status md_force(md_box* b, double* force_out, double* epot, double* virial)
+{
+    if (!b || !b->lj_set) return fail(b, MD_ERR_ARG, "md_force: md_set_lj not called");
+    CKS(enter(b));
+    CKS(ensure_thermo(b, 1));
+    CKS(clear_err(b));
+    CKS(enqueue_force(b, 1, b->d_thermo));
+    if (force_out && b->ntot > 0) {
+        size_t fb = sizeof(double) * 3 * (size_t)b->ntot;
+        if (is_device_ptr(force_out)) {
+            CK(b, launch_force_out(b->d, force_out, lch(b)));
+        } else {
+            CKS(ensure_stage(b, fb));
+            CK(b, launch_force_out(b->d, static_cast<double*>(b->d_stage), lch(b)));
+            CK(b, cudaMemcpyAsync(force_out, b->d_stage, fb, cudaMemcpyDeviceToHost, b->stream));
+        }
+    }
+    std::vector<double> th(4 * (size_t)b->nrep);
+    CK(b, cudaMemcpyAsync(th.data(), b->d_thermo, sizeof(double) * th.size(), cudaMemcpyDeviceToHost,
+                          b->stream));
+    int e2[2];
+    CKS(read_err(b, e2));
+    CKS(leave(b));
+    for (int r = 0; r < b->nrep; ++r) {
+        if (epot) epot[r] = th[4 * r + 0];
+        if (virial) virial[r] = th[4 * r + 2];
+    }
+    if (e2[0] & LJ_ERRBIT_NONFINITE) return fail(b, MD_ERR_NONFINITE, "md_force: non-finite force");
+    return MD_OK;
+}
+
+md_status md_integrate(md_box* b, double dt, int64_t nsteps, int32_t ckpt_every, double* thermo_out)
+{
+    if (!b || !b->lj_set) return fail(b, MD_ERR_ARG, "md_integrate: md_set_lj not called");
+    if (!(dt > 0.0) || nsteps < 0 || ckpt_every < 0) return fail(b, MD_ERR_ARG, "md_integrate: bad arguments");
+    if (ckpt_every > 0) return fail(b, MD_ERR_ARG, "md_integrate: recording not available");
+    if (nsteps == 0) return MD_OK;
+    CKS(enter(b));
+    b->fresh_abs = false;   // offsets advance; xabs keeps the last build
+    const int energy = thermo_out ? 1 : 0;
+    const int64_t chunk = b->chunk_steps;
+    if (energy) CKS(ensure_thermo(b, std::min(nsteps, chunk)));
+    bool out_dev = energy && is_device_ptr(thermo_out);
+    int64_t done = 0;
+    int retries = 0;
+    while (done < nsteps) {
+        int64_t n = std::min(chunk, nsteps - done);
+        CKS(clear_err(b));
+        CKS(snapshot(b, false));
+        cudaGraphExec_t g;
+        CKS(get_graph(b, n, dt, energy, &g));
+        CK(b, cudaGraphLaunch(g, b->stream));
+        int e2[2];
+        CKS(read_err(b, e2));
+        for (auto& ge : b->graphs)
+            if (ge.exec == g) {
+                b->launches += ge.kernels;
+                for (size_t k = 0; k < ge.used.size(); ++k)
+                    if (ge.used[k]) {
+                        float ms = 0.f;
+                        CK(b, cudaEventElapsedTime(&ms, ge.ev[2 * k], ge.ev[2 * k + 1]));
+                        b->prof_ms[k % 4] += ms;
+                        b->prof_n[k % 4] += 1;
+                    }
+            }
+        if (e2[0] & LJ_ERRBIT_CAPACITY) {
+            if (++retries > 8) return fail(b, MD_ERR_CAPACITY, "md_integrate: list keeps overflowing");
+            CKS(snapshot(b, true));
+            int K = round_up((int64_t)(e2[1] * 1.15) + 8, 8);
+            CKS(alloc_lists(b, std::max(K, b->d.K + 8)));
+            CKS(full_rebuild(b));
+            continue;
+        }
+        if (e2[0] & LJ_ERRBIT_NONFINITE) {
+            CKS(leave(b));
+            return fail(b, MD_ERR_NONFINITE, "md_integrate: non-finite force");
+        }
+        if (energy) {
+            size_t cnt = (size_t)n * b->nrep * 4;
+            double* dst = thermo_out + (size_t)done * b->nrep * 4;
+            CK(b, cudaMemcpyAsync(dst, b->d_thermo, sizeof(double) * cnt,
+                                  out_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, b->stream));
+        }
+        done += n;
+        b->steps += n;
+    }
+    CKS(leave(b));
+    return MD_OK;
+}
+
+md_status md_adjoint(md_box* b, const double*, const double*, double*, double*, double*, double*)
+{
+    return fail(b, MD_ERR_STATE, "md_adjoint: no recorded forward run");
+}
+
+md_status md_get_state(md_box* b, double* pos, double* vel, int32_t* image)
+{
+    if (!b) return MD_ERR_ARG;
+    if (b->ntot == 0) return MD_OK;
+    if (!b->binned) return fail(b, MD_ERR_ARG, "md_get_state: md_set_lj not called");
+    CKS(enter(b));
+    size_t pb = sizeof(double) * 3 * (size_t)b->ntot, ib = sizeof(int) * 3 * (size_t)b->ntot;
+    bool dp = is_device_ptr(pos), dv = is_device_ptr(vel), di = is_device_ptr(image);
+    CKS(ensure_stage(b, 2 * pb + ib));
+    char* st = static_cast<char*>(b->d_stage);
+    double* tp = pos ? (dp ? pos : reinterpret_cast<double*>(st)) : nullptr;
+    double* tv = vel ? (dv ? vel : reinterpret_cast<double*>(st + pb)) : nullptr;
+    int* ti = image ? (di ? image : reinterpret_cast<int*>(st + 2 * pb)) : nullptr;
+    CK(b, launch_download(b->d, tp, tv, ti, lch(b)));
+    if (pos && !dp) CK(b, cudaMemcpyAsync(pos, tp, pb, cudaMemcpyDeviceToHost, b->stream));
+    if (vel && !dv) CK(b, cudaMemcpyAsync(vel, tv, pb, cudaMemcpyDeviceToHost, b->stream));
+    if (image && !di) CK(b, cudaMemcpyAsync(image, ti, ib, cudaMemcpyDeviceToHost, b->stream));
+    CKS(leave(b));
+    return MD_OK;
+}
+
+md_status md_set_state(md_box* b, const double* pos, const double* vel)
+{
+    if (!b || (!pos && b->ntot > 0)) return MD_ERR_ARG;
+    if (b->ntot == 0) return MD_OK;
+    CKS(enter(b));
+    size_t pb = sizeof(double) * 3 * (size_t)b->ntot;
+    CKS(ensure_stage(b, 3 * pb));
+    char* st = static_cast<char*>(b->d_stage);
+    const void* dpos;
+    CKS(input_ptr(b, pos, pb, &dpos, 0));
+    const double* dvel = nullptr;
+    if (vel) {
+        const void* v;
+        CKS(input_ptr(b, vel, pb, &v, pb));
+        dvel = static_cast<const double*>(v);
+    } else if (b->binned) {
+        // keep the velocities: bring them to user order first
+        double* tv = reinterpret_cast<double*>(st + 2 * pb);
+        CK(b, launch_download(b->d, nullptr, tv, nullptr, lch(b)));
+        dvel = tv;
+    }
+    if (dpos == st + 2 * pb) return fail(b, MD_ERR_ARG, "internal staging overlap");
+    CK(b, launch_upload(b->d, static_cast<const double*>(dpos), dvel, b->d_type_user,
+                        (vel || b->binned) ? 1 : 0, lch(b)));
+    b->fresh_abs = true;
+    if (b->lj_set) CKS(full_rebuild(b));
+    CKS(leave(b));
+    return MD_OK;
+}
+
+md_status md_get_nlist(md_box* b, int32_t* count, int64_t* nbr, int64_t cap, double* pos)
+{
+    if (!b || !count || (nbr && cap < 1)) return MD_ERR_ARG;
+    if (!b->lj_set) return fail(b, MD_ERR_ARG, "md_get_nlist: md_set_lj not called");
+    if (b->ntot == 0) return MD_OK;
+    CKS(enter(b));
+    size_t cb = sizeof(int) * (size_t)b->ntot;
+    size_t nb = nbr ? sizeof(int64_t) * (size_t)b->ntot * (size_t)cap : 0;
+    size_t pb = pos ? sizeof(double) * 3 * (size_t)b->ntot : 0;
+    CKS(ensure_stage(b, cb + nb + pb + 512));
+    char* st = static_cast<char*>(b->d_stage);
+    int* tc = reinterpret_cast<int*>(st);
+    long long* tn = nbr ? reinterpret_cast<long long*>(st + ((cb + 255) & ~(size_t)255)) : nullptr;
+    double* tp = pos ? reinterpret_cast<double*>(st + ((cb + 255) & ~(size_t)255) + ((nb + 255) & ~(size_t)255))
+                     : nullptr;
+    CK(b, launch_get_nlist(b->d, tc, tn, (long long)cap, tp, lch(b)));
+    std::vector<int> hc(b->ntot);
+    CK(b, cudaMemcpyAsync(hc.data(), tc, cb, cudaMemcpyDeviceToHost, b->stream));
+    if (nbr) CK(b, cudaMemcpyAsync(nbr, tn, nb, is_device_ptr(nbr) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, b->stream));
+    if (pos) CK(b, cudaMemcpyAsync(pos, tp, pb, is_device_ptr(pos) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, b->stream));
+    CKS(leave(b));
+    int mx = 0;
+    for (int v : hc) mx = std::max(mx, v);
+    if (is_device_ptr(count)) {
+        CK(b, cudaMemcpy(count, hc.data(), cb, cudaMemcpyHostToDevice));
+    } else {
+        std::memcpy(count, hc.data(), cb);
+    }
+    if (mx > b->d.K) return fail(b, MD_ERR_CAPACITY, "md_get_nlist: list truncated at capacity");
+    if (nbr && mx > cap) return fail(b, MD_ERR_CAPACITY, "md_get_nlist: cap too small");
+    return MD_OK;
+}
+
+md_status md_get_info(md_box* b, md_info* out)
+{
+    if (!b || !out) return MD_ERR_ARG;
+    md_info i{};
+    i.n_total = b->ntot;
+    i.nrep = b->nrep;
+    i.ntypes = b->nt;
+    i.capacity = b->d.K;
+    i.precision = b->prec;
+    i.ncell_total = b->d.ncell;
+    i.steps = b->steps;
+    int64_t bytes = 0;
+    for (auto& a : b->allocs) bytes += (int64_t)a.bytes;
+    i.device_bytes = bytes;
+    i.rlist = b->rl;
+    i.launches = b->launches;
+    if (b->lj_set) {
+        std::vector<unsigned long long> nb(b->nrep);
+        CK(b, cudaSetDevice(b->device));
+        CK(b, cudaMemcpyAsync(nb.data(), b->d.nbuild, sizeof(unsigned long long) * b->nrep,
+                              cudaMemcpyDeviceToHost, b->stream));
+        CK(b, cudaStreamSynchronize(b->stream));
+        for (auto v : nb) i.rebuilds += (int64_t)v;
+        std::vector<int> cnt(b->np);
+        CK(b, cudaMemcpyAsync(cnt.data(), b->d.nbr_count, sizeof(int) * b->np, cudaMemcpyDeviceToHost,
+                              b->stream));
+        CK(b, cudaStreamSynchronize(b->stream));
+        for (int c : cnt) i.list_entries += c;
+    }
+    *out = i;
+    return MD_OK;
+}
+
+md_status md_set_profiling(md_box* b, int32_t on)
+{
+    if (!b) return MD_ERR_ARG;
+    b->profiling = on != 0;
+    for (int k = 0; k < 4; ++k) {
+        b->prof_ms[k] = 0.0;
+        b->prof_n[k] = 0;
+    }
+    invalidate_graphs(b);
+    return MD_OK;
+}
+
+md_status md_get_profile(md_box* b, double* ms, int64_t* launches)
+{
+    if (!b) return MD_ERR_ARG;
+    for (int k = 0; k < 4; ++k) {
+        if (ms) ms[k] = b->prof_ms[k];
+        if (launches) launches[k] = b->prof_n[k];
+    }
+    return MD_OK;
+}
+
+md_status md_set_tuning(md_box* b, int32_t block_force, int32_t block_list, int32_t capacity)
+{
+    if (!b || capacity < 0) return MD_ERR_ARG;
+    (void)block_force;
+    (void)block_list;
+    b->min_capacity = capacity;
+    if (capacity > 0 && b->lj_set) {
+        // re-layout the lists at this capacity now (they regrow on overflow)
+        CKS(enter(b));
+        CKS(alloc_lists(b, round_up(capacity, 1)));
+        CKS(full_rebuild(b));
+        CKS(leave(b));
+    }
+    return MD_OK;
+}
+
+}  // extern "C"

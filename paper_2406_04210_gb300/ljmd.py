@@ -1,0 +1,311 @@
+"""Thin ctypes binding of libljmd.so (the C ABI of include/ljmd.h).
+
+Argument marshalling only: every step of the MD path runs in the library's
+CUDA kernels.  Array arguments may be numpy arrays (host) or torch CUDA
+tensors (device); results are returned as numpy arrays unless a torch tensor
+is passed to be filled.  Device memory of a box comes from PyTorch's caching
+allocator through the library's allocator hook, and calls are ordered on the
+current torch CUDA stream.
+
+The library is loaded on first use; a missing library raises
+:class:`LibraryMissing` (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "_build", "libljmd.so")
+
+PREC = {"mixed_ds": 0, "mixed_fp64": 1, "fp64": 2}
+STATUS = {0: "MD_OK", 1: "MD_ERR_ARG", 2: "MD_ERR_CUDA", 3: "MD_ERR_OOM", 4: "MD_ERR_CAPACITY",
+          5: "MD_ERR_BOX_TOO_SMALL", 6: "MD_ERR_NONFINITE", 7: "MD_ERR_TIMEOUT",
+          8: "MD_ERR_STATE"}
+
+EXPORTS = ["md_set_allocator", "md_batch_create", "md_box_create", "md_box_destroy",
+           "md_set_lj", "md_neighbour_update", "md_force", "md_integrate", "md_adjoint",
+           "md_get_state", "md_set_state", "md_get_nlist", "md_get_info", "md_set_tuning",
+           "md_set_profiling", "md_get_profile", "md_last_error", "md_status_string"]
+
+
+class LibraryMissing(RuntimeError):
+    pass
+
+
+class MDError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n_total", ctypes.c_int64), ("nrep", ctypes.c_int32),
+                ("ntypes", ctypes.c_int32), ("capacity", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("ncell_total", ctypes.c_int64),
+                ("rebuilds", ctypes.c_int64), ("steps", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64), ("rlist", ctypes.c_double),
+                ("launches", ctypes.c_int64), ("list_entries", ctypes.c_int64)]
+
+
+_lock = threading.Lock()
+_lib = None
+_ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_FREE = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+_cb = []
+
+
+def library_path() -> str:
+    return _SO
+
+
+def load(path: str | None = None):
+    """Load libljmd.so (raises LibraryMissing if it was not built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or _SO
+        if not os.path.exists(p):
+            raise LibraryMissing(
+                f"{p} is missing: build it with `python -m paper_2406_04210_gb300.build`")
+        L = ctypes.CDLL(p)
+        vp, i32, i64, d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        L.md_set_allocator.argtypes = [_ALLOC, _FREE, vp]
+        L.md_batch_create.argtypes = [ctypes.POINTER(vp), i32, vp, vp, vp, vp, vp, i32, vp]
+        L.md_box_create.argtypes = [ctypes.POINTER(vp), i64, vp, vp, vp, vp, i32, vp]
+        L.md_box_destroy.argtypes = [vp]
+        L.md_set_lj.argtypes = [vp, i32, vp, vp, vp, d, i32]
+        L.md_neighbour_update.argtypes = [vp, i32, vp]
+        L.md_force.argtypes = [vp, vp, vp, vp]
+        L.md_integrate.argtypes = [vp, d, i64, i32, vp]
+        L.md_adjoint.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        L.md_get_state.argtypes = [vp, vp, vp, vp]
+        L.md_set_state.argtypes = [vp, vp, vp]
+        L.md_get_nlist.argtypes = [vp, vp, vp, i64, vp]
+        L.md_get_info.argtypes = [vp, ctypes.POINTER(Info)]
+        L.md_set_tuning.argtypes = [vp, i32, i32, i32]
+        L.md_set_profiling.argtypes = [vp, i32]
+        L.md_get_profile.argtypes = [vp, vp, vp]
+        L.md_last_error.argtypes = [vp]
+        L.md_last_error.restype = ctypes.c_char_p
+        L.md_status_string.argtypes = [i32]
+        L.md_status_string.restype = ctypes.c_char_p
+        for name in EXPORTS:
+            if name not in ("md_last_error", "md_status_string"):
+                getattr(L, name).restype = i32
+        _lib = L
+        _install_torch_allocator(L)
+        return L
+
+
+def _install_torch_allocator(L):
+    """Route the library's device allocations through torch's caching allocator."""
+    try:
+        import torch
+    except ImportError:
+        return
+    if not torch.cuda.is_available():
+        return
+
+    def _alloc(nbytes, ctx):
+        try:
+            return int(torch.cuda.caching_allocator_alloc(int(nbytes)))
+        except Exception:   # out of memory: report NULL to the library
+            return 0
+
+    def _free(ptr, ctx):
+        try:
+            torch.cuda.caching_allocator_delete(int(ptr))
+        except Exception:
+            pass
+
+    a, f = _ALLOC(_alloc), _FREE(_free)
+    _cb.extend([a, f])
+    L.md_set_allocator(a, f, None)
+
+
+def _ptr(x):
+    """(pointer, keepalive) of a numpy array or torch tensor; None -> NULL."""
+    if x is None:
+        return None, None
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            x = np.ascontiguousarray(x)
+        return x.ctypes.data, x
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor arguments must be contiguous")
+        return x.data_ptr(), x
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+def _stream_handle(stream=None):
+    try:
+        import torch
+        if torch.cuda.is_available():
+            s = stream if stream is not None else torch.cuda.current_stream()
+            return s.cuda_stream
+    except ImportError:
+        pass
+    return None
+
+
+class Box:
+    """A batch of nrep periodic LJ boxes advanced by libljmd on one GPU."""
+
+    def __init__(self, pos, box, vel=None, type=None, n=None, precision="mixed_ds",
+                 stream=None):
+        L = load()
+        box = np.ascontiguousarray(np.atleast_2d(np.asarray(box, dtype=np.float64)))
+        nrep = box.shape[0]
+        if n is None:
+            if nrep != 1:
+                raise ValueError("n (particles per replica) is required for nrep > 1")
+            n = [int(pos.shape[0])]
+        n = np.ascontiguousarray(np.asarray(n, dtype=np.int64))
+        self.nrep, self.n_total = nrep, int(n.sum())
+        self.n = n
+        pos = _as_f64(pos)
+        vel = _as_f64(vel) if vel is not None else None
+        type = _as_i32(type) if type is not None else None
+        pp, kp = _ptr(pos)
+        pv, kv = _ptr(vel)
+        pt, kt = _ptr(type)
+        h = ctypes.c_void_p()
+        st = L.md_batch_create(ctypes.byref(h), nrep, n.ctypes.data, box.ctypes.data, pt, pp,
+                               pv, PREC[precision], _stream_handle(stream))
+        if st != 0:
+            raise MDError(st, "md_batch_create failed")
+        self._h = h
+        self._lib = L
+        self.precision = precision
+        self.box = box
+
+    # -- helpers --
+    def _check(self, st, what):
+        if st != 0:
+            raise MDError(st, f"{what}: {self._lib.md_last_error(self._h).decode()}")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.md_box_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- ABI wrappers --
+    def set_lj(self, eps=1.0, sigma=1.0, rcut=2.5, skin=0.3, shift=True):
+        eps = np.ascontiguousarray(np.atleast_2d(eps), dtype=np.float64)
+        sigma = np.ascontiguousarray(np.atleast_2d(sigma), dtype=np.float64)
+        rcut = np.ascontiguousarray(np.atleast_2d(rcut), dtype=np.float64)
+        nt = eps.shape[0]
+        self._check(self._lib.md_set_lj(self._h, nt, eps.ctypes.data, sigma.ctypes.data,
+                                        rcut.ctypes.data, float(skin), 1 if shift else 0),
+                    "md_set_lj")
+        return self
+
+    def neighbour_update(self, force=False):
+        r = ctypes.c_int32(0)
+        self._check(self._lib.md_neighbour_update(self._h, 1 if force else 0, ctypes.byref(r)),
+                    "md_neighbour_update")
+        return r.value
+
+    def force(self, out=None):
+        f = np.zeros((self.n_total, 3)) if out is None else out
+        e = np.zeros(self.nrep)
+        w = np.zeros(self.nrep)
+        pf, kf = _ptr(f)
+        self._check(self._lib.md_force(self._h, pf, e.ctypes.data, w.ctypes.data), "md_force")
+        return f, e, w
+
+    def integrate(self, dt, nsteps, thermo=True, ckpt_every=0, out=None):
+        th = None
+        if thermo:
+            th = np.zeros((nsteps, self.nrep, 4)) if out is None else out
+        pt, kt = _ptr(th)
+        self._check(self._lib.md_integrate(self._h, float(dt), int(nsteps), int(ckpt_every), pt),
+                    "md_integrate")
+        return th
+
+    def adjoint(self, lam_x, lam_v, out=None):
+        lx0 = np.zeros((self.n_total, 3))
+        lv0 = np.zeros((self.n_total, 3))
+        info = self.info()
+        ge = np.zeros((info.ntypes, info.ntypes))
+        gs = np.zeros((info.ntypes, info.ntypes))
+        a, ka = _ptr(_as_f64(lam_x))
+        b, kb = _ptr(_as_f64(lam_v))
+        self._check(self._lib.md_adjoint(self._h, a, b, lx0.ctypes.data, lv0.ctypes.data,
+                                         ge.ctypes.data, gs.ctypes.data), "md_adjoint")
+        return lx0, lv0, ge, gs
+
+    def get_state(self):
+        pos = np.zeros((self.n_total, 3))
+        vel = np.zeros((self.n_total, 3))
+        img = np.zeros((self.n_total, 3), dtype=np.int32)
+        self._check(self._lib.md_get_state(self._h, pos.ctypes.data, vel.ctypes.data,
+                                           img.ctypes.data), "md_get_state")
+        return pos, vel, img
+
+    def set_state(self, pos, vel=None):
+        pp, kp = _ptr(_as_f64(pos))
+        pv, kv = _ptr(_as_f64(vel) if vel is not None else None)
+        self._check(self._lib.md_set_state(self._h, pp, pv), "md_set_state")
+
+    def nlist(self, cap=None):
+        count = np.zeros(self.n_total, dtype=np.int32)
+        info = self.info()
+        cap = cap or info.capacity
+        nbr = np.full((self.n_total, cap), -1, dtype=np.int64)
+        pos = np.zeros((self.n_total, 3))
+        self._check(self._lib.md_get_nlist(self._h, count.ctypes.data, nbr.ctypes.data, cap,
+                                           pos.ctypes.data), "md_get_nlist")
+        return count, nbr, pos
+
+    def info(self) -> Info:
+        i = Info()
+        self._check(self._lib.md_get_info(self._h, ctypes.byref(i)), "md_get_info")
+        return i
+
+    def set_tuning(self, block_force=0, block_list=0, capacity=0):
+        self._check(self._lib.md_set_tuning(self._h, block_force, block_list, capacity),
+                    "md_set_tuning")
+
+    def set_profiling(self, on=True):
+        self._check(self._lib.md_set_profiling(self._h, 1 if on else 0), "md_set_profiling")
+
+    PHASES = ("integrate", "list_update", "force", "thermo")
+
+    def profile(self):
+        ms = np.zeros(4)
+        cnt = np.zeros(4, dtype=np.int64)
+        self._check(self._lib.md_get_profile(self._h, ms.ctypes.data, cnt.ctypes.data),
+                    "md_get_profile")
+        return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(self.PHASES)}
+
+
+def _as_f64(a):
+    if a is None or hasattr(a, "data_ptr"):
+        return a
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _as_i32(a):
+    if a is None or hasattr(a, "data_ptr"):
+        return a
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def from_system(s, precision="mixed_ds"):
+    """Box from an inputs.System, with its LJ parameters set."""
+    b = Box(s.pos, s.box, s.vel, s.type, precision=precision)
+    b.set_lj(s.eps, s.sigma, s.rcut, s.skin, True)
+    return b

@@ -1,0 +1,282 @@
+"""GPU parity of the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (written here, derived in DESIGN.md "Tolerances"):
+  * neighbour sets: identical to the oracle's FP64 definition (bit-exact
+    membership, compared after sorting by user index) in every precision;
+  * forces: max_i |F_i - F_i^oracle| / S_i <= 1e-5 (FP32 pair forces) and
+    <= 1e-12 (FP64), S_i = sum_j |F_ij| the per-particle sum of pair-force
+    magnitudes (the scale of the sum F_i = sum_j F_ij);
+  * E_pot: relative 1e-5 (FP32) / 1e-12 (FP64); W (a sum of terms of both
+    signs that crosses zero as a fluid equilibrates): |dW| <= tol * W_abs
+    with W_abs = sum_{i<j} |f_ij| r_ij^2 <= rc/2 sum_i S_i;
+  * 10-step trajectories: max min-image |dx| <= 1e-4 sigma and
+    max |dv| <= 1e-4 v_rms.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2406_04210_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+PRECS = ["mixed_ds", "mixed_fp64", "fp64"]
+FTOL = {"mixed_ds": 1e-5, "mixed_fp64": 1e-5, "fp64": 1e-12}
+ETOL = {"mixed_ds": 1e-5, "mixed_fp64": 1e-5, "fp64": 1e-12}
+
+
+@pytest.fixture(scope="module")
+def ljmd():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2406_04210_gb300 import build, ljmd as m
+    build.build()
+    m.load()
+    return m
+
+
+def _lj(s):
+    return oracle.LJ(s.eps, s.sigma, s.rcut, True)
+
+
+def pair_scale(box, pos, lj, types=None):
+    """S_i = sum_j |F_ij| over pairs within the cutoff (oracle pair function)."""
+    from scipy.spatial import cKDTree
+    n = pos.shape[0]
+    t = np.zeros(n, np.int32) if types is None else types
+    tree = cKDTree(np.mod(pos, box), boxsize=box)
+    pairs = tree.query_pairs(float(lj.rcut.max()) + 1e-9, output_type="ndarray")
+    d = pos[pairs[:, 0]] - pos[pairs[:, 1]]
+    d -= box * np.rint(d / box)
+    r2 = np.sum(d * d, axis=1)
+    S = np.zeros(n)
+    for k, (i, j) in enumerate(pairs):
+        f = oracle.pair(lj.eps[t[i], t[j]], lj.sigma[t[i], t[j]], lj.rcut[t[i], t[j]], 1, r2[k])[0]
+        m = abs(f) * np.sqrt(r2[k])
+        S[i] += m
+        S[j] += m
+    return S
+
+
+def thermo_close(th, ref, wabs, tol=1e-5):
+    """Per-step (E_pot, E_kin, W, T) against the oracle's."""
+    np.testing.assert_allclose(th[:, [0, 1, 3]], ref[:, [0, 1, 3]], rtol=tol, atol=1e-8)
+    assert np.abs(th[:, 2] - ref[:, 2]).max() <= tol * wabs
+
+
+def check_lists(b, s, rl):
+    count, nbr, pos_used = b.nlist()
+    np.testing.assert_array_equal(pos_used, np.mod(s.pos, s.box))   # built from the inputs
+    ref = oracle.nlist(s.box, pos_used, rl, use_cells=True)
+    assert np.array_equal(count, ref.count)
+    for i in range(s.n):
+        got = np.sort(nbr[i, : count[i]])
+        assert np.array_equal(got, ref.list[i, : ref.count[i]]), i
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_lj4000_lists_forces_energy(ljmd, prec):
+    s = inputs.lj4000()
+    b = ljmd.from_system(s, prec)
+    check_lists(b, s, 2.5 + 0.3)
+    f, e, w = b.force()
+    lj = _lj(s)
+    fo, eo, wo = oracle.forces(s.box, s.pos, lj)
+    S = pair_scale(s.box, s.pos, lj)
+    err = np.linalg.norm(f - fo, axis=1) / S
+    assert err.max() <= FTOL[prec], err.max()
+    assert abs(e[0] - eo) <= ETOL[prec] * abs(eo)
+    assert abs(w[0] - wo) <= ETOL[prec] * 0.5 * 2.5 * S.sum()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_lj4000_ten_steps(ljmd, prec):
+    s = inputs.lj4000()
+    b = ljmd.from_system(s, prec)
+    th = b.integrate(s.dt, 10)
+    pos, vel, img = b.get_state()
+    r = oracle.run(s.box, s.pos, s.vel, _lj(s), s.skin, s.dt, 10)
+    d = pos - r["pos"]
+    d -= s.box * np.rint(d / s.box)
+    vrms = np.sqrt(np.mean(s.vel ** 2))
+    assert np.abs(d).max() <= 1e-4
+    assert np.abs(vel - r["vel"]).max() <= 1e-4 * vrms
+    np.testing.assert_array_equal(img, r["img"])
+    # thermo after every step: E_pot, E_kin, W, T
+    wabs = 0.5 * 2.5 * pair_scale(s.box, s.pos, _lj(s)).sum()
+    thermo_close(th[:, 0, :], r["thermo"], wabs)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_lj4000_rebuild_parity_after_motion(ljmd, prec):
+    # lists rebuilt during a run still equal the FP64 definition at the
+    # positions they were built from
+    s = inputs.lj4000()
+    b = ljmd.from_system(s, prec)
+    b.integrate(s.dt, 60, thermo=False)
+    assert b.info().rebuilds >= 2
+    b.neighbour_update(force=True)
+    count, nbr, pos_used = b.nlist()
+    ref = oracle.nlist(s.box, pos_used, 2.8)
+    assert np.array_equal(count, ref.count)
+    for i in range(s.n):
+        assert np.array_equal(np.sort(nbr[i, : count[i]]), ref.list[i, : ref.count[i]])
+
+
+def test_binary_mixture_parity(ljmd):
+    s = inputs.binary_random_system(n=3000, seed=17)
+    lj = _lj(s)
+    pos, it, fmax = oracle.fire(s.box, s.pos, lj, s.type, maxit=300, ftol=1e-2)
+    s.pos = pos
+    for prec in PRECS:
+        b = ljmd.from_system(s, prec)
+        rl = float(s.rcut.max()) + s.skin
+        check_lists(b, s, rl)
+        f, e, w = b.force()
+        fo, eo, wo = oracle.forces(s.box, s.pos, lj, s.type)
+        S = pair_scale(s.box, s.pos, lj, s.type)
+        assert (np.linalg.norm(f - fo, axis=1) / S).max() <= FTOL[prec]
+        assert abs(e[0] - eo) <= ETOL[prec] * abs(eo)
+        th = b.integrate(s.dt, 10)
+        r = oracle.run(s.box, s.pos, s.vel, lj, s.skin, s.dt, 10, type_=s.type)
+        p2, v2, _ = b.get_state()
+        d = p2 - r["pos"]
+        d -= s.box * np.rint(d / s.box)
+        assert np.abs(d).max() <= 1e-4
+
+
+@pytest.mark.parametrize("n,L", [(1, 9.0), (2, 9.0), (60, 5.7), (200, 8.5), (700, 8.41)])
+def test_small_and_degenerate_boxes(ljmd, n, L):
+    # 1-2 particles, 2 cells per dimension (L < 3 rl) and exactly 3 cells
+    rng = np.random.default_rng(n)
+    box = np.array([L, L, L])
+    pos = rng.uniform(0, L, size=(n, 3)) if n > 2 else np.array([[0.1, 1, 1], [L - 0.9, 1, 1]])[:n]
+    if n > 2:
+        pos, _, _ = oracle.fire(box, pos, oracle.LJ.single(), maxit=200, ftol=1.0)
+    vel = rng.normal(0, 0.5, size=(n, 3))
+    b = ljmd.Box(pos, box, vel, precision="fp64")
+    b.set_lj(1.0, 1.0, 2.5, 0.3)
+    s = inputs.System(box, pos, vel, np.zeros(n, np.int32), np.ones((1, 1)), np.ones((1, 1)),
+                      np.full((1, 1), 2.5))
+    check_lists(b, s, 2.8)
+    f, e, w = b.force()
+    fo, eo, wo = oracle.forces_brute(box, pos, oracle.LJ.single())
+    np.testing.assert_allclose(f, fo, rtol=0, atol=1e-11 * max(1.0, np.abs(fo).max()))
+
+
+def test_cell_faces_and_boundaries(ljmd):
+    # particles exactly on cell faces, at x = 0 and just below L
+    rl = 2.8
+    L = 3 * rl
+    box = np.array([L, L, L])
+    g = np.arange(0, L, rl / 2)
+    pos = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    pos[::5, 1] = np.nextafter(L, 0)
+    n = pos.shape[0]
+    b = ljmd.Box(pos, box, None, precision="mixed_ds")
+    b.set_lj(1.0, 1.0, 2.5, 0.3)
+    s = inputs.System(box, pos, np.zeros((n, 3)), np.zeros(n, np.int32), np.ones((1, 1)),
+                      np.ones((1, 1)), np.full((1, 1), 2.5))
+    check_lists(b, s, rl)
+
+
+def test_batched_replicas_match_single_boxes(ljmd):
+    systems = inputs.replica_systems(nrep=6, nmin=500, nmax=3000, seed=5)
+    n = [x.n for x in systems]
+    pos = np.concatenate([x.pos for x in systems])
+    vel = np.concatenate([x.vel for x in systems])
+    box = np.stack([x.box for x in systems])
+    b = ljmd.Box(pos, box, vel, n=n, precision="mixed_ds")
+    b.set_lj(1.0, 1.0, 2.5, 0.3)
+    f, e, w = b.force()
+    th = b.integrate(0.005, 10)
+    p2, v2, _ = b.get_state()
+    o = 0
+    for r, x in enumerate(systems):
+        lj = _lj(x)
+        fo, eo, wo = oracle.forces(x.box, x.pos, lj)
+        S = pair_scale(x.box, x.pos, lj)
+        assert (np.linalg.norm(f[o:o + x.n] - fo, axis=1) / S).max() <= 1e-5
+        assert abs(e[r] - eo) <= 1e-5 * abs(eo)
+        rr = oracle.run(x.box, x.pos, x.vel, lj, 0.3, 0.005, 10)
+        d = p2[o:o + x.n] - rr["pos"]
+        d -= x.box * np.rint(d / x.box)
+        assert np.abs(d).max() <= 1e-4
+        thermo_close(th[:, r, :], rr["thermo"], 0.5 * 2.5 * S.sum())
+        o += x.n
+
+
+def test_capacity_overflow_recovers(ljmd):
+    s = inputs.lj4000()
+    ref = ljmd.from_system(s, "mixed_ds")
+    th_ref = ref.integrate(s.dt, 200)
+    b = ljmd.from_system(s, "mixed_ds")
+    count, _, _ = b.nlist()
+    b.set_tuning(capacity=int(count.max()))     # exactly full: a later build overflows
+    k0 = b.info().capacity
+    th = b.integrate(s.dt, 200)
+    assert b.info().capacity > k0
+    # same trajectory up to FP32 summation order
+    np.testing.assert_allclose(th[:, 0, 0], th_ref[:, 0, 0], rtol=1e-4)
+    # a capacity below the largest list forces an immediate regrow
+    b.set_tuning(capacity=8)
+    assert b.info().capacity > 8
+    check_lists(b, inputs.System(s.box, b.nlist()[2], s.vel, s.type, s.eps, s.sigma, s.rcut),
+                2.8)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_energy_conservation(ljmd, prec):
+    s = inputs.fcc_system(8, seed=3)    # 2048 particles
+    b = ljmd.from_system(s, prec)
+    th = b.integrate(s.dt, 2000)
+    E = th[:, 0, 0] + th[:, 0, 1]
+    assert np.abs(E - E[0]).max() / s.n < 5e-4
+    # no systematic drift beyond the fluctuation level
+    slope = np.polyfit(np.arange(E.size) * s.dt, E / s.n, 1)[0]
+    assert abs(slope) < 1e-4
+
+
+def test_deterministic(ljmd):
+    s = inputs.lj4000()
+    out = []
+    for _ in range(2):
+        b = ljmd.from_system(s, "mixed_ds")
+        th = b.integrate(s.dt, 50)
+        out.append((b.get_state()[0], th))
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+
+
+def test_set_state_roundtrip(ljmd):
+    s = inputs.lj4000()
+    b = ljmd.from_system(s, "mixed_fp64")
+    b.integrate(s.dt, 20, thermo=False)
+    p, v, _ = b.get_state()
+    c = ljmd.from_system(s, "mixed_fp64")
+    c.set_state(p, v)
+    np.testing.assert_allclose(c.get_state()[0], np.mod(p, s.box), rtol=0, atol=1e-12)
+    fa, ea, _ = b.force()
+    fb, eb, _ = c.force()
+    assert abs(ea[0] - eb[0]) < 1e-5 * abs(ea[0])
+
+
+def test_box_too_small_rejected(ljmd):
+    b = ljmd.Box(np.zeros((4, 3)) + 1.0, [5.0, 5.0, 5.0])
+    with pytest.raises(ljmd.MDError) as ei:
+        b.set_lj(1.0, 1.0, 2.5, 0.3)
+    assert ei.value.status == 5
+
+
+def test_torch_device_arrays(ljmd):
+    import torch
+    s = inputs.lj4000()
+    pos = torch.tensor(s.pos, device="cuda")
+    vel = torch.tensor(s.vel, device="cuda")
+    b = ljmd.Box(pos, s.box, vel, precision="mixed_ds")
+    b.set_lj(1.0, 1.0, 2.5, 0.3)
+    out = torch.zeros((s.n, 3), dtype=torch.float64, device="cuda")
+    b.force(out=out)
+    fh, _, _ = b.force()
+    np.testing.assert_array_equal(out.cpu().numpy(), fh)
