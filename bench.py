@@ -198,7 +198,7 @@ def run_gpu(args):
     ljmd.load()
 
     # independent replica per rank (replicas only: the path does not shard)
-    s = inputs.fcc_system(100, seed=inputs.SEEDS["lj4m"] + rank)
+    s = inputs.fcc_system(args.ncell, seed=inputs.SEEDS["lj4m"] + rank)
     n = s.n
     box = ljmd.from_system(s, "mixed_ds")
     thermo = torch.zeros((max(args.steps, args.warmup, 1), 1, 4), dtype=torch.float64,
@@ -262,7 +262,7 @@ def run_gpu(args):
 
     # other precisions on the same workload
     prec = {"mixed_ds": value / world}
-    for p, k in (("mixed_fp64", args.steps), ("fp64", max(20, args.steps // 10))):
+    for p, k in (() if args.quick else (("mixed_fp64", args.steps), ("fp64", max(20, args.steps // 10)))):
         b2 = ljmd.from_system(s, p)
         b2.integrate(s.dt, min(args.warmup, 10) or 1, thermo=True, out=thermo[:10])
         ms2 = timed_integrate(b2, s.dt, k, thermo[:k])
@@ -276,7 +276,7 @@ def run_gpu(args):
         return
 
     cpu = None
-    if world == 1:
+    if world == 1 and not args.quick:
         ps, ns, st, sec = oracle_sample(10, ncell=40)
         cpu = {"value": ps, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"fcc 40^3 x 4 = {ns} particles of the workload's fluid, {st} "
@@ -316,9 +316,17 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=100)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--ncell", type=int, default=100,
+                    help="fcc cells per edge (100 = the 4.0M-particle workload; smaller for profiling)")
+    ap.add_argument("--quick", action="store_true",
+                    help="skip the other precisions and the CPU oracle (profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.ncell != 100:
+        n = 4 * args.ncell ** 3
+        WORKLOAD["workload"] = WORKLOAD["workload"].replace("100^3 x 4 = 4,000,000", f"{args.ncell}^3 x 4 = {n:,}")
+        WORKLOAD["n_particles"] = n
     if args.impl == "reference":
         run_reference(args)
     else:

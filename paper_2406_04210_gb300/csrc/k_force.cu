@@ -20,8 +20,8 @@ __device__ __forceinline__ double warp_sum_d(double v)
     return v;
 }
 
-// Sum two doubles over the block (blockDim == LJ_CHUNK); valid in thread 0.
-__device__ __forceinline__ void block_sum2(double& a, double& c, double (*s)[LJ_CHUNK / 32])
+// Sum two doubles over the block; valid in thread 0.
+__device__ __forceinline__ void block_sum2(double& a, double& c, double (*s)[32])
 {
     a = warp_sum_d(a);
     c = warp_sum_d(c);
@@ -34,7 +34,7 @@ __device__ __forceinline__ void block_sum2(double& a, double& c, double (*s)[LJ_
     if (threadIdx.x == 0) {
         a = 0.0;
         c = 0.0;
-        for (int k = 0; k < LJ_CHUNK / 32; ++k) {
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
             a += s[0][k];
             c += s[1][k];
         }
@@ -42,88 +42,172 @@ __device__ __forceinline__ void block_sum2(double& a, double& c, double (*s)[LJ_
     __syncthreads();
 }
 
-__device__ __forceinline__ void load_shift_table(float4* s_shift, const RepDev& R)
+// Per-segment prologue shared by the pair kernels: tile ranges, image-shift
+// table of the replica, and (first segment of a replica) the reset of the
+// rebuild triggers, which the list update of this step has consumed.
+__device__ __forceinline__ void seg_prologue(const BoxDev& b, int w, int4 sg, const RepDev& R,
+                                             Tile& t, float4* s_shift, int& cur_r, bool reset)
 {
-    if (threadIdx.x < 27) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        seg_tile(b, R, sg, t);
+        if (reset && w == 0) *b.any_req = 0;   // the list update has run
+        if (reset && w == R.seg_off) {
+            b.disp_max[sg.x] = 0u;
+            b.rebuild_req[sg.x] = 0;
+        }
+    }
+    if (sg.x != cur_r && threadIdx.x < 27) {
         int k = threadIdx.x;
         s_shift[k] = make_float4((float)(k % 3 - 1) * R.ellf[0], (float)((k / 3) % 3 - 1) * R.ellf[1],
                                  (float)(k / 9 - 1) * R.ellf[2], 0.f);
     }
+    cur_r = sg.x;
+    __syncthreads();
 }
 
-// FP32 force.  MONO: a single species, parameters in registers.
+// One pair term of the FP32 force: accumulates f d into (fx, fy, fz) and,
+// with ENERGY, the pair energy and virial; the term is masked (not branched)
+// by the cutoff test, so threads of a particle never diverge.
 template <bool MONO, bool ENERGY>
-__global__ void __launch_bounds__(LJ_CHUNK) k_force_f32(BoxDev b)
+__device__ __forceinline__ void pair_f32(unsigned ent, const float4& pi, int ti, const float4* s_tile,
+                                         const float4* s_shift, const float4* s_lj, const float* s_rc2,
+                                         const float* s_esh, int nt, const float4& mlj, float mrc2,
+                                         float mesh, float& fx, float& fy, float& fz, float& e, float& vir)
 {
-    __shared__ float4 s_shift[27];
-    __shared__ float4 s_par[LJ_MAXT * LJ_MAXT];   // sig2, eps48, eps4, shift
+    const float4 pj = s_tile[ent & LJ_TILE_MASK];
+    const float4 sh = s_shift[ent >> LJ_TILE_BITS];
+    const float dx = (pi.x - pj.x) - sh.x;
+    const float dy = (pi.y - pj.y) - sh.y;
+    const float dz = (pi.z - pj.z) - sh.z;
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    float4 c;
+    float rc2, esh;
+    if (MONO) {
+        c = mlj;
+        rc2 = mrc2;
+        esh = mesh;
+    } else {
+        const int pp = ti * nt + __float_as_int(pj.w);
+        c = s_lj[pp];
+        rc2 = s_rc2[pp];
+        esh = ENERGY ? s_esh[pp] : 0.f;
+    }
+    const float r2i = __fdividef(1.0f, r2);
+    const float r6i = r2i * r2i * r2i;
+    float f = r2i * r6i * fmaf(c.x, r6i, -c.y);   // c = (48 eps s^12, 24 eps s^6, 4 eps s^12, 4 eps s^6)
+    const bool in = r2 < rc2;
+    f = in ? f : 0.f;
+    fx = fmaf(f, dx, fx);
+    fy = fmaf(f, dy, fy);
+    fz = fmaf(f, dz, fz);
+    if (ENERGY) {
+        const float u = r6i * fmaf(c.z, r6i, -c.w) - esh;
+        e += in ? u : 0.f;
+        vir = fmaf(f, r2, vir);
+    }
+}
+
+// FP32 pair force over one segment per block, LJ_TPP threads per particle.
+// The tile's FP32 offsets and the segment's list block (rows of K entries of
+// its particles, contiguous) are staged in shared memory by bulk copies; the
+// 8 threads of a particle take entries s, s+8, ... of its list (two at a time
+// for instruction-level parallelism) and combine their partial forces with
+// shuffles.  MONO: a single species, parameters in registers.
+template <bool MONO, bool ENERGY, bool LSM>
+__device__ __forceinline__ void force_segment_f32(const BoxDev& b, int n, int p0, const float4* s_tile,
+                                                  const uint16_t* s_list, const float4* s_shift,
+                                                  const float4* s_lj, const float* s_rc2, const float* s_esh,
+                                                  int nt, const float4& mlj, float mrc2, float mesh, float& e,
+                                                  float& vir)
+{
+    const int K = b.K;
+    const int grp = threadIdx.x / LJ_TPP, l8 = threadIdx.x % LJ_TPP;
+    for (int base = 0; base < n; base += LJ_SEG_THREADS / LJ_TPP) {
+        const int il = base + grp;
+        const bool act = il < n;
+        const int p = p0 + il;
+        float4 pi = make_float4(0.f, 0.f, 0.f, 0.f);
+        int cnt = 0;
+        if (act) {
+            pi = b.posq[p];
+            cnt = min(b.nbr_count[p], K);
+        }
+        const int ti = __float_as_int(pi.w);
+        const uint16_t* L = LSM ? s_list + (size_t)il * K : b.nbr + (size_t)K * p;
+        float fx = 0.f, fy = 0.f, fz = 0.f, fx2 = 0.f, fy2 = 0.f, fz2 = 0.f;
+        int s = l8;
+        for (; s + LJ_TPP < cnt; s += 2 * LJ_TPP) {
+            const unsigned e0 = L[s], e1 = L[s + LJ_TPP];
+            pair_f32<MONO, ENERGY>(e0, pi, ti, s_tile, s_shift, s_lj, s_rc2, s_esh, nt, mlj, mrc2, mesh, fx, fy, fz, e, vir);
+            pair_f32<MONO, ENERGY>(e1, pi, ti, s_tile, s_shift, s_lj, s_rc2, s_esh, nt, mlj, mrc2, mesh, fx2, fy2, fz2, e, vir);
+        }
+        if (s < cnt)
+            pair_f32<MONO, ENERGY>(L[s], pi, ti, s_tile, s_shift, s_lj, s_rc2, s_esh, nt, mlj, mrc2, mesh, fx, fy, fz, e, vir);
+        fx += fx2;
+        fy += fy2;
+        fz += fz2;
+#pragma unroll
+        for (int o = LJ_TPP / 2; o > 0; o >>= 1) {
+            fx += __shfl_xor_sync(0xffffffffu, fx, o);
+            fy += __shfl_xor_sync(0xffffffffu, fy, o);
+            fz += __shfl_xor_sync(0xffffffffu, fz, o);
+        }
+        if (act && l8 == 0) {
+            b.force4[p] = make_float4(fx, fy, fz, 0.f);
+            if (!isfinite(fx + fy + fz)) atomicOr(&b.err[0], LJ_ERRBIT_NONFINITE);
+        }
+    }
+}
+
+template <bool MONO, bool ENERGY>
+__global__ void __launch_bounds__(LJ_SEG_THREADS, 3) k_force_f32(BoxDev b)
+{
+    extern __shared__ __align__(16) unsigned char dsm[];
+    float4* s_tile = reinterpret_cast<float4*>(dsm);
+    uint16_t* s_list = reinterpret_cast<uint16_t*>(dsm + LJ_TILE_MAX * 16);
+    __shared__ float4 s_shift[32];
+    __shared__ Tile s_t;
+    __shared__ __align__(8) unsigned long long s_bar;
+    __shared__ float4 s_lj[LJ_MAXT * LJ_MAXT];   // c12, c6, e12, e6
     __shared__ float s_rc2[LJ_MAXT * LJ_MAXT];
-    __shared__ double s_red[2][LJ_CHUNK / 32];
+    __shared__ float s_esh[LJ_MAXT * LJ_MAXT];
+    __shared__ double s_red[2][32];
     const LJDev* lj = b.lj;
     const int nt = lj->nt;
     for (int k = threadIdx.x; k < nt * nt; k += blockDim.x) {
-        s_par[k] = make_float4(lj->sig2[k], lj->eps48[k], lj->eps4[k], lj->shift[k]);
+        s_lj[k] = make_float4(lj->c12[k], lj->c6[k], lj->e12[k], lj->e6[k]);
         s_rc2[k] = lj->rc2[k];
+        s_esh[k] = lj->shift[k];
     }
-    const float m_sig2 = lj->sig2[0], m_eps48 = lj->eps48[0], m_eps4 = lj->eps4[0],
-                m_shift = lj->shift[0], m_rc2 = lj->rc2[0];
+    if (threadIdx.x >= 27 && threadIdx.x < 32) s_shift[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 mlj = make_float4(lj->c12[0], lj->c6[0], lj->e12[0], lj->e6[0]);
+    const float mrc2 = lj->rc2[0];
+    const float mesh = lj->shift[0];
+    if (threadIdx.x == 0) mbar_init(&s_bar, 1);
+    unsigned phase = 0;
     int cur_r = -1;
-    for (int w = blockIdx.x; w < b.nchunk; w += gridDim.x) {
-        int4 ch = b.chunk[w];
-        int r = ch.x;
-        const RepDev& R = b.rep[r];
-        if (r != cur_r) {
-            __syncthreads();
-            load_shift_table(s_shift, R);
-            __syncthreads();
-            cur_r = r;
-        }
-        if (threadIdx.x == 0 && ch.y == R.p_off) {
-            // the list of this replica is now used: clear the rebuild triggers
-            b.disp_max[r] = 0u;
-            b.rebuild_req[r] = 0;
-        }
-        int p = ch.y + (int)threadIdx.x;
-        float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f, vir = 0.f;
-        if (p < ch.z) {
-            float4 pi = b.posq[p];
-            int ti = __float_as_int(pi.w);
-            int cnt = min(b.nbr_count[p], b.K);
-            const uint32_t* lp = b.nbr + (size_t)(p >> 5) * (size_t)b.K * 32 + (p & 31);
-#pragma unroll 4
-            for (int s = 0; s < cnt; ++s) {
-                uint32_t ent = __ldcs(lp + (size_t)s * 32);
-                int j = (int)(ent & LJ_IDX_MASK);
-                float4 sh = s_shift[ent >> LJ_IDX_BITS];
-                float4 pj = __ldg(&b.posq[j]);
-                float dx = (pi.x - pj.x) - sh.x;
-                float dy = (pi.y - pj.y) - sh.y;
-                float dz = (pi.z - pj.z) - sh.z;
-                float r2 = dx * dx + dy * dy + dz * dz;
-                float sig2, eps48, eps4, shv, rc2;
-                if (MONO) {
-                    sig2 = m_sig2; eps48 = m_eps48; eps4 = m_eps4; shv = m_shift; rc2 = m_rc2;
-                } else {
-                    int pp = ti * nt + __float_as_int(pj.w);
-                    float4 q = s_par[pp];
-                    sig2 = q.x; eps48 = q.y; eps4 = q.z; shv = q.w; rc2 = s_rc2[pp];
-                }
-                if (r2 < rc2) {
-                    float r2i = __frcp_rn(r2);
-                    float s2 = sig2 * r2i;
-                    float s6 = s2 * s2 * s2;
-                    float f = eps48 * r2i * s6 * (s6 - 0.5f);
-                    fx += f * dx;
-                    fy += f * dy;
-                    fz += f * dz;
-                    if (ENERGY) {
-                        e += eps4 * s6 * (s6 - 1.0f) - shv;
-                        vir += f * r2;
-                    }
-                }
-            }
-            b.force4[p] = make_float4(fx, fy, fz, 0.f);
-            if (!isfinite(fx + fy + fz)) atomicOr(&b.err[0], LJ_ERRBIT_NONFINITE);
+    const int K = b.K;
+    for (int w = blockIdx.x; w < b.nseg; w += gridDim.x) {
+        int4 sg = b.seg[w];
+        const RepDev& R = b.rep[sg.x];
+        seg_prologue(b, w, sg, R, s_t, s_shift, cur_r, true);
+        const int n = s_t.n, p0 = s_t.p0;
+        const bool ok = s_t.total <= LJ_TILE_MAX;   // else flagged by k_nlist
+        const unsigned list_bytes = (unsigned)n * (unsigned)K * 2u;
+        const bool lsm = ok && list_bytes <= LJ_LIST_SMEM;
+        if (ok && s_t.total + n > 0 &&
+            !stage_tile_bulk(b.posq, s_t, s_tile, &s_bar, phase, b.err, s_list,
+                             b.nbr + (size_t)K * p0, lsm ? list_bytes : 0u))
+            return;
+        float e = 0.f, vir = 0.f;
+        if (ok) {
+            if (lsm)
+                force_segment_f32<MONO, ENERGY, true>(b, n, p0, s_tile, s_list, s_shift, s_lj, s_rc2, s_esh, nt,
+                                                      mlj, mrc2, mesh, e, vir);
+            else
+                force_segment_f32<MONO, ENERGY, false>(b, n, p0, s_tile, s_list, s_shift, s_lj, s_rc2, s_esh, nt,
+                                                       mlj, mrc2, mesh, e, vir);
         }
         if (ENERGY) {
             double de = 0.5 * (double)e, dw = 0.5 * (double)vir;
@@ -136,46 +220,52 @@ __global__ void __launch_bounds__(LJ_CHUNK) k_force_f32(BoxDev b)
     }
 }
 
-// FP64 force from the FP64 cell-relative offsets (MD_PREC_FP64).
+// FP64 pair force (MD_PREC_FP64): same lists; the tile holds slot indices
+// and the FP64 offsets are read from global memory.
 template <bool ENERGY>
-__global__ void __launch_bounds__(LJ_CHUNK) k_force_f64(BoxDev b)
+__global__ void __launch_bounds__(LJ_F64_THREADS) k_force_f64(BoxDev b)
 {
+    __shared__ int s_slot[LJ_TILE_MAX];
+    __shared__ float4 s_shift[27];
     __shared__ double s_sh[3][27];
-    __shared__ double s_red[2][LJ_CHUNK / 32];
+    __shared__ Tile s_t;
+    __shared__ double s_red[2][32];
     const LJDev* lj = b.lj;
     const int nt = lj->nt;
     const int np = b.np;
     int cur_r = -1;
-    for (int w = blockIdx.x; w < b.nchunk; w += gridDim.x) {
-        int4 ch = b.chunk[w];
-        int r = ch.x;
-        const RepDev& R = b.rep[r];
-        if (r != cur_r) {
-            __syncthreads();
-            if (threadIdx.x < 27) {
-                int k = threadIdx.x;
-                s_sh[0][k] = (double)(k % 3 - 1) * R.ell[0];
-                s_sh[1][k] = (double)((k / 3) % 3 - 1) * R.ell[1];
-                s_sh[2][k] = (double)(k / 9 - 1) * R.ell[2];
+    for (int w = blockIdx.x; w < b.nseg; w += gridDim.x) {
+        int4 sg = b.seg[w];
+        const RepDev& R = b.rep[sg.x];
+        int prev = cur_r;
+        seg_prologue(b, w, sg, R, s_t, s_shift, cur_r, true);
+        if (sg.x != prev && threadIdx.x < 27) {
+            int k = threadIdx.x;
+            s_sh[0][k] = (double)(k % 3 - 1) * R.ell[0];
+            s_sh[1][k] = (double)((k / 3) % 3 - 1) * R.ell[1];
+            s_sh[2][k] = (double)(k / 9 - 1) * R.ell[2];
+        }
+        const int n = s_t.n, p0 = s_t.p0;
+        const bool ok = s_t.total <= LJ_TILE_MAX;
+        if (ok) {
+            for (int q = 0; q < 18; ++q) {
+                int beg = s_t.beg[q], len = s_t.end[q] - beg, base = s_t.base[q];
+                for (int t = threadIdx.x; t < len; t += blockDim.x) s_slot[base + t] = beg + t;
             }
-            __syncthreads();
-            cur_r = r;
         }
-        if (threadIdx.x == 0 && ch.y == R.p_off) {
-            b.disp_max[r] = 0u;
-            b.rebuild_req[r] = 0;
-        }
-        int p = ch.y + (int)threadIdx.x;
-        double fx = 0.0, fy = 0.0, fz = 0.0, e = 0.0, vir = 0.0;
-        if (p < ch.z) {
+        __syncthreads();
+        double e = 0.0, vir = 0.0;
+        for (int il = threadIdx.x; il < n && ok; il += blockDim.x) {
+            int p = p0 + il;
             double xi = b.off[p], yi = b.off[np + p], zi = b.off[2 * np + p];
             int ti = b.type[p];
             int cnt = min(b.nbr_count[p], b.K);
-            const uint32_t* lp = b.nbr + (size_t)(p >> 5) * (size_t)b.K * 32 + (p & 31);
+            const uint16_t* lp = b.nbr + (size_t)b.K * p;
+            double fx = 0.0, fy = 0.0, fz = 0.0;
             for (int s = 0; s < cnt; ++s) {
-                uint32_t ent = __ldcs(lp + (size_t)s * 32);
-                int j = (int)(ent & LJ_IDX_MASK);
-                int k = (int)(ent >> LJ_IDX_BITS);
+                unsigned ent = __ldcs(lp + s);
+                int j = s_slot[ent & LJ_TILE_MASK];
+                int k = (int)(ent >> LJ_TILE_BITS);
                 double dx = (xi - __ldg(&b.off[j])) - s_sh[0][k];
                 double dy = (yi - __ldg(&b.off[np + j])) - s_sh[1][k];
                 double dz = (zi - __ldg(&b.off[2 * np + j])) - s_sh[2][k];
@@ -211,54 +301,77 @@ __global__ void __launch_bounds__(LJ_CHUNK) k_force_f64(BoxDev b)
     }
 }
 
-// One warp per replica: E_pot, E_kin, W, T from the per-chunk partial sums,
-// in a fixed order (deterministic).
-__global__ void k_thermo(BoxDev b, double* out, int with_kin)
+// One block per replica: E_pot, E_kin, W, T from the per-chunk partial sums,
+// summed in a fixed order (deterministic): thread t takes chunks t, t+B, ...
+__global__ void __launch_bounds__(512) k_thermo(BoxDev b, double* out, int with_kin)
 {
-    const int lane = threadIdx.x & 31;
-    const int wpb = blockDim.x >> 5;
-    for (int r = blockIdx.x * wpb + (threadIdx.x >> 5); r < b.nrep; r += gridDim.x * wpb) {
+    __shared__ double s_red[3][512 / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int r = blockIdx.x; r < b.nrep; r += gridDim.x) {
         const RepDev& R = b.rep[r];
         double e = 0.0, w = 0.0, k = 0.0;
-        for (int c = R.chunk_off + lane; c < R.chunk_off + R.nchunk; c += 32) {
+        for (int c = R.seg_off + (int)threadIdx.x; c < R.seg_off + R.nseg; c += blockDim.x) {
             e += b.part_f[2 * c];
             w += b.part_f[2 * c + 1];
-            if (with_kin) k += b.part_k[c];
         }
+        if (with_kin)
+            for (int c = R.chunk_off + (int)threadIdx.x; c < R.chunk_off + R.nchunk; c += blockDim.x)
+                k += b.part_k[c];
         e = warp_sum_d(e);
         w = warp_sum_d(w);
         k = warp_sum_d(k);
         if (lane == 0) {
+            s_red[0][warp] = e;
+            s_red[1][warp] = w;
+            s_red[2][warp] = k;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            e = w = k = 0.0;
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+                e += s_red[0][q];
+                w += s_red[1][q];
+                k += s_red[2][q];
+            }
             out[4 * r + 0] = e;
             out[4 * r + 1] = k;
             out[4 * r + 2] = w;
             out[4 * r + 3] = R.n > 1 ? 2.0 * k / (3.0 * (double)R.n - 3.0) : 0.0;
         }
+        __syncthreads();
     }
 }
 
 }  // namespace
 
+template <bool MONO, bool ENERGY>
+static cudaError_t launch_f32(const BoxDev& b, Launch l)
+{
+    const int dyn = LJ_TILE_MAX * 16 + LJ_LIST_SMEM;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_force_f32<MONO, ENERGY>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_force_f32<MONO, ENERGY><<<l.grid, LJ_SEG_THREADS, dyn, l.s>>>(b);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_force(const BoxDev& b, int energy, Launch l)
 {
     if (b.prec == 2) {
-        if (energy) k_force_f64<true><<<l.grid, LJ_CHUNK, 0, l.s>>>(b);
-        else k_force_f64<false><<<l.grid, LJ_CHUNK, 0, l.s>>>(b);
-    } else {
-        bool mono = b.nt == 1;
-        if (mono) {
-            if (energy) k_force_f32<true, true><<<l.grid, LJ_CHUNK, 0, l.s>>>(b);
-            else k_force_f32<true, false><<<l.grid, LJ_CHUNK, 0, l.s>>>(b);
-        } else {
-            if (energy) k_force_f32<false, true><<<l.grid, LJ_CHUNK, 0, l.s>>>(b);
-            else k_force_f32<false, false><<<l.grid, LJ_CHUNK, 0, l.s>>>(b);
-        }
+        if (energy) k_force_f64<true><<<l.grid, LJ_F64_THREADS, 0, l.s>>>(b);
+        else k_force_f64<false><<<l.grid, LJ_F64_THREADS, 0, l.s>>>(b);
+        return cudaGetLastError();
     }
-    return cudaGetLastError();
+    if (b.nt == 1) return energy ? launch_f32<true, true>(b, l) : launch_f32<true, false>(b, l);
+    return energy ? launch_f32<false, true>(b, l) : launch_f32<false, false>(b, l);
 }
 
 cudaError_t launch_thermo(const BoxDev& b, double* out, int with_kin, Launch l)
 {
-    k_thermo<<<l.grid, 128, 0, l.s>>>(b, out, with_kin);
+    k_thermo<<<l.grid, 512, 0, l.s>>>(b, out, with_kin);
     return cudaGetLastError();
 }

@@ -105,8 +105,10 @@ __global__ void __launch_bounds__(LJ_CHUNK) k_integrate(BoxDev b, double dt)
         }
         if (MODE != LJ_STEP_LAST) {
             unsigned m = __reduce_max_sync(0xffffffffu, dmax);
-            if ((threadIdx.x & 31) == 0 && __uint_as_float(m) > b.disp_thr2)
+            if ((threadIdx.x & 31) == 0 && __uint_as_float(m) > b.disp_thr2) {
                 atomicMax(&b.disp_max[r], m);
+                atomicOr(b.any_req, 1);
+            }
         }
         if (ENERGY && MODE != LJ_STEP_FIRST) {
             double s = warp_sum_d(0.5 * ek);
@@ -239,26 +241,35 @@ __global__ void __launch_bounds__(LJ_CHUNK) k_force_out(BoxDev b, double* f)
     }
 }
 
-__global__ void __launch_bounds__(LJ_CHUNK) k_get_nlist(BoxDev b, int* count, long long* nbr,
-                                                        long long cap, double* pos)
+__global__ void __launch_bounds__(LJ_SEG_THREADS) k_get_nlist(BoxDev b, int* count, long long* nbr,
+                                                              long long cap, double* pos)
 {
+    __shared__ Tile s_t;
     const int np = b.np;
-    for (int w = blockIdx.x; w < b.nchunk; w += gridDim.x) {
-        int4 ch = b.chunk[w];
-        int p = ch.y + (int)threadIdx.x;
-        if (p >= ch.z) continue;
-        long long gu = b.uid[p];
-        int cnt = b.nbr_count[p];
-        count[gu] = cnt;
-        if (pos)
-            for (int c = 0; c < 3; ++c) pos[3 * gu + c] = b.xabs[c * np + p];
-        if (nbr) {
-            int m = cnt < b.K ? cnt : b.K;
-            if ((long long)m > cap) m = (int)cap;
-            const uint32_t* lp = b.nbr + (size_t)(p >> 5) * (size_t)b.K * 32 + (p & 31);
-            for (int s = 0; s < m; ++s) {
-                int j = (int)(lp[(size_t)s * 32] & LJ_IDX_MASK);
-                nbr[gu * cap + s] = b.uid[j];
+    for (int w = blockIdx.x; w < b.nseg; w += gridDim.x) {
+        int4 sg = b.seg[w];
+        __syncthreads();
+        if (threadIdx.x == 0) seg_tile(b, b.rep[sg.x], sg, s_t);
+        __syncthreads();
+        const int n = s_t.n, p0 = s_t.p0;
+        for (int il = threadIdx.x; il < n; il += blockDim.x) {
+            int p = p0 + il;
+            long long gu = b.uid[p];
+            int cnt = b.nbr_count[p];
+            count[gu] = cnt;
+            if (pos)
+                for (int c = 0; c < 3; ++c) pos[3 * gu + c] = b.xabs[c * np + p];
+            if (nbr && s_t.total <= LJ_TILE_MAX) {
+                int m = cnt < b.K ? cnt : b.K;
+                if ((long long)m > cap) m = (int)cap;
+                const uint16_t* lp = b.nbr + (size_t)b.K * p;
+                for (int s = 0; s < m; ++s) {
+                    int idx = lp[s] & LJ_TILE_MASK;
+                    int q = 0;
+                    while (q < 17 && idx >= s_t.base[q] + (s_t.end[q] - s_t.beg[q])) ++q;
+                    int j = s_t.beg[q] + (idx - s_t.base[q]);
+                    nbr[gu * cap + s] = b.uid[j];
+                }
             }
         }
     }
@@ -295,7 +306,7 @@ cudaError_t launch_force_out(const BoxDev& b, double* f, Launch l)
 cudaError_t launch_get_nlist(const BoxDev& b, int* count, long long* nbr, long long cap,
                              double* pos, Launch l)
 {
-    k_get_nlist<<<l.grid, LJ_CHUNK, 0, l.s>>>(b, count, nbr, cap, pos);
+    k_get_nlist<<<l.grid, LJ_SEG_THREADS, 0, l.s>>>(b, count, nbr, cap, pos);
     return cudaGetLastError();
 }
 

@@ -61,6 +61,7 @@ __device__ __forceinline__ double load_off(const BoxDev& b, int c, int p)
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(LJ_CHUNK) k_bin(BoxDev b, int from_abs)
 {
+    if (!box_needs_rebuild(b)) return;
     for (int w = blockIdx.x; w < b.nchunk; w += gridDim.x) {
         int4 ch = b.chunk[w];
         int r = ch.x;
@@ -149,6 +150,7 @@ __device__ __forceinline__ int block_excl_scan(int v, int* s_warp, int& total)
 __global__ void __launch_bounds__(1024) k_scan_tiles(BoxDev b, const int4* tiles, int ntiles,
                                                       int* tile_sum)
 {
+    if (!box_needs_rebuild(b)) return;
     __shared__ int s_warp[33];
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         int4 tl = tiles[t];
@@ -169,6 +171,7 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(BoxDev b, const int4* tiles
 __global__ void __launch_bounds__(256) k_scan_add(BoxDev b, const int4* tiles, int ntiles,
                                                    const int* tile_sum)
 {
+    if (!box_needs_rebuild(b)) return;
     __shared__ int s_off;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         int4 tl = tiles[t];
@@ -195,6 +198,7 @@ __global__ void __launch_bounds__(256) k_scan_add(BoxDev b, const int4* tiles, i
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(LJ_CHUNK) k_scatter(BoxDev b)
 {
+    if (!box_needs_rebuild(b)) return;
     for (int w = blockIdx.x; w < b.nchunk; w += gridDim.x) {
         int4 ch = b.chunk[w];
         if (!rep_needs_rebuild(b, ch.x)) continue;
@@ -212,6 +216,7 @@ __global__ void __launch_bounds__(LJ_CHUNK) k_scatter(BoxDev b)
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_sortgather(BoxDev b)
 {
+    if (!box_needs_rebuild(b)) return;
     const int lane = threadIdx.x & 31;
     const int wpb = blockDim.x >> 5;
     for (int gc = blockIdx.x * wpb + (threadIdx.x >> 5); gc < b.ncell; gc += gridDim.x * wpb) {
@@ -271,11 +276,13 @@ __global__ void __launch_bounds__(256) k_sortgather(BoxDev b)
 }
 
 // ---------------------------------------------------------------------------
-// k_nlist: Verlet list of every particle of a rebuilding replica (Sec. 3).
-// Membership |d_ij|^2 < rl^2 is decided in FP32 from the cell-relative
-// offsets; pairs within `band` of rl^2 are re-decided in FP64 from the
-// wrapped positions with the minimum image, in the same operation order as
-// the plain definition, so the lists equal the FP64 definition exactly.
+// k_nlist: Verlet list of every particle of a rebuilding replica (Sec. 3),
+// one segment per block.  The segment's tile (its 27-cell neighbourhood) is
+// staged in shared memory and candidates are read from there.  Membership
+// |d_ij|^2 < rl^2 is decided in FP32 from the cell-relative offsets; pairs
+// within `band` of rl^2 are re-decided in FP64 from the wrapped positions
+// with the minimum image, in the same operation order as the plain
+// definition, so the lists equal the FP64 definition exactly.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ bool exact_within(const BoxDev& b, const RepDev& R, int p, int j)
 {
@@ -291,65 +298,107 @@ __device__ __forceinline__ bool exact_within(const BoxDev& b, const RepDev& R, i
     return d2 < b.rl2;
 }
 
-__global__ void __launch_bounds__(LJ_CHUNK) k_nlist(BoxDev b)
+__global__ void __launch_bounds__(LJ_LIST_THREADS) k_nlist(BoxDev b)
 {
-    __shared__ float4 s_shift[27];
+    if (!box_needs_rebuild(b)) return;
+    __shared__ __align__(16) float4 s_tile[LJ_TILE_MAX];
+    __shared__ float4 s_shift[32];
+    __shared__ int4 s_rng[LJ_SEG_MAX_CELLS * 27];   // (first, end, tile offset) per (cell, k)
+    __shared__ Tile s_t;
+    __shared__ __align__(8) unsigned long long s_bar;
+    if (threadIdx.x == 0) mbar_init(&s_bar, 1);
+    unsigned phase = 0;
     int cur_r = -1;
     const float lo2 = b.rl2f - b.band, hi2 = b.rl2f + b.band;
-    for (int w = blockIdx.x; w < b.nchunk; w += gridDim.x) {
-        int4 ch = b.chunk[w];
-        int r = ch.x;
+    // LJ_TPP threads per particle: lanes l8 of group grp share the particle
+    const int grp = threadIdx.x / LJ_TPP, l8 = threadIdx.x % LJ_TPP;
+    const int gshift = (threadIdx.x & 31) & ~(LJ_TPP - 1);
+    const unsigned gmask = ((1u << LJ_TPP) - 1u) << gshift;
+    for (int w = blockIdx.x; w < b.nseg; w += gridDim.x) {
+        int4 sg = b.seg[w];
+        int r = sg.x;
         if (!rep_needs_rebuild(b, r)) continue;   // block-uniform
         const RepDev& R = b.rep[r];
-        if (r != cur_r) {
-            __syncthreads();
-            if (threadIdx.x < 27) {
-                int k = threadIdx.x;
-                s_shift[k] = make_float4((float)(k % 3 - 1) * R.ellf[0],
-                                         (float)((k / 3) % 3 - 1) * R.ellf[1],
-                                         (float)(k / 9 - 1) * R.ellf[2], 0.f);
-            }
-            __syncthreads();
-            cur_r = r;
+        __syncthreads();                          // previous segment done
+        if (threadIdx.x == 0) {
+            seg_tile(b, R, sg, s_t);
+            if (w == R.seg_off) atomicAdd(&b.nbuild[r], 1ull);
         }
-        if (threadIdx.x == 0 && ch.y == R.p_off) atomicAdd(&b.nbuild[r], 1ull);
-        int p = ch.y + (int)threadIdx.x;
-        if (p >= ch.z) continue;
-        float4 pi = b.posq[p];
-        int cx, cy;
-        int cz = cell_coords(R, b.cell[p], cx, cy);
-        uint32_t* out = b.nbr + (size_t)(p >> 5) * (size_t)b.K * 32 + (p & 31);
-        int cnt = 0;
-        for (int k = 0; k < 27; ++k) {
-            int dx = k % 3 - 1, dy = (k / 3) % 3 - 1, dz = k / 9 - 1;
-            int nx = cx + dx, ny = cy + dy, nz = cz + dz;
-            nx = nx < 0 ? nx + R.nc[0] : (nx >= R.nc[0] ? nx - R.nc[0] : nx);
-            ny = ny < 0 ? ny + R.nc[1] : (ny >= R.nc[1] ? ny - R.nc[1] : ny);
-            nz = nz < 0 ? nz + R.nc[2] : (nz >= R.nc[2] ? nz - R.nc[2] : nz);
-            int cn = R.cell_off + nx + R.nc[0] * (ny + R.nc[1] * nz);
-            int js = b.cell_start[cn], je = b.cell_end[cn];
-            float4 sh = s_shift[k];
-            for (int j = js; j < je; ++j) {
-                if (j == p && k == 13) continue;
-                float4 pj = b.posq[j];
-                float ddx = (pi.x - pj.x) - sh.x;
-                float ddy = (pi.y - pj.y) - sh.y;
-                float ddz = (pi.z - pj.z) - sh.z;
-                float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                bool in;
-                if (r2 < lo2) in = true;
-                else if (r2 >= hi2) in = false;
-                else in = exact_within(b, R, p, j);
-                if (in) {
-                    if (cnt < b.K) out[(size_t)cnt * 32] = ((uint32_t)k << LJ_IDX_BITS) | (uint32_t)j;
-                    ++cnt;
+        if (r != cur_r && threadIdx.x < 32) {
+            int k = threadIdx.x;
+            s_shift[k] = k < 27 ? make_float4((float)(k % 3 - 1) * R.ellf[0], (float)((k / 3) % 3 - 1) * R.ellf[1],
+                                              (float)(k / 9 - 1) * R.ellf[2], 0.f)
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        cur_r = r;
+        __syncthreads();
+        const int n = s_t.n, p0 = s_t.p0;
+        if (s_t.total > LJ_TILE_MAX) {
+            if (threadIdx.x == 0) atomicOr(&b.err[0], LJ_ERRBIT_TILE);
+            for (int il = threadIdx.x; il < n; il += blockDim.x) b.nbr_count[p0 + il] = 0;
+            continue;
+        }
+        // neighbour-cell ranges of the segment's cells, with their tile offsets
+        const int nx = R.nc[0], ny = R.nc[1], nz = R.nc[2];
+        const int cy = sg.z % ny, cz = sg.z / ny;
+        const int c0 = R.cell_off + sg.y + nx * sg.z;
+        for (int idx = threadIdx.x; idx < sg.w * 27; idx += blockDim.x) {
+            const int cl = idx / 27, k = idx % 27;
+            const int dx = k % 3 - 1, dy = (k / 3) % 3 - 1, dz = k / 9 - 1;
+            const int cn = R.cell_off + wrapi(sg.y + cl + dx, nx) + nx * (wrapi(cy + dy, ny) + ny * wrapi(cz + dz, nz));
+            const int js = b.cell_start[cn], je = b.cell_end[cn];
+            int q = 2 * (3 * (dz + 1) + (dy + 1));
+            if (!(js >= s_t.beg[q] && js < s_t.end[q])) ++q;
+            s_rng[idx] = make_int4(js, je, s_t.base[q] - s_t.beg[q], 0);
+        }
+        if (s_t.total > 0 && !stage_tile_bulk(b.posq, s_t, s_tile, &s_bar, phase, b.err)) return;
+        const float ell_h[3] = {0.5f * R.ellf[0], 0.5f * R.ellf[1], 0.5f * R.ellf[2]};
+        const float rcull = b.rl2f + b.band;
+        for (int base = 0; base < n; base += LJ_LIST_THREADS / LJ_TPP) {
+            const int il = base + grp;
+            if (il >= n) continue;                // group-uniform
+            const int p = p0 + il;
+            const float4 pi = b.posq[p];
+            const int4* rng = s_rng + (b.cell[p] - c0) * 27;
+            uint16_t* out = b.nbr + (size_t)b.K * p;
+            int cnt = 0;
+            for (int k = 0; k < 27; ++k) {
+                const int4 rk = rng[k];
+                const int js = rk.x, je = rk.y, toff = rk.z;
+                if (js == je) continue;
+                // skip the cell if its box lies beyond the list radius
+                const float4 sh = s_shift[k];
+                const float gx = fmaxf(fabsf(pi.x - sh.x) - ell_h[0], 0.f);
+                const float gy = fmaxf(fabsf(pi.y - sh.y) - ell_h[1], 0.f);
+                const float gz = fmaxf(fabsf(pi.z - sh.z) - ell_h[2], 0.f);
+                if (gx * gx + gy * gy + gz * gz >= rcull) continue;
+                for (int jb = js; jb < je; jb += LJ_TPP) {
+                    const int j = jb + l8;
+                    bool in = false;
+                    if (j < je && !(j == p && k == 13)) {
+                        const float4 pj = s_tile[j + toff];
+                        const float ddx = (pi.x - pj.x) - sh.x;
+                        const float ddy = (pi.y - pj.y) - sh.y;
+                        const float ddz = (pi.z - pj.z) - sh.z;
+                        const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                        if (r2 < lo2) in = true;
+                        else if (r2 < hi2) in = exact_within(b, R, p, j);
+                    }
+                    const unsigned bits = (__ballot_sync(gmask, in) >> gshift) & ((1u << LJ_TPP) - 1u);
+                    if (in) {
+                        const int pos = cnt + __popc(bits & ((1u << l8) - 1u));
+                        if (pos < b.K) out[pos] = (uint16_t)((k << LJ_TILE_BITS) | (j + toff));
+                    }
+                    cnt += __popc(bits);
                 }
             }
-        }
-        b.nbr_count[p] = cnt;
-        if (cnt > b.K) {
-            atomicOr(&b.err[0], LJ_ERRBIT_CAPACITY);
-            atomicMax(&b.err[1], cnt);
+            if (l8 == 0) {
+                b.nbr_count[p] = cnt;
+                if (cnt > b.K) {
+                    atomicOr(&b.err[0], LJ_ERRBIT_CAPACITY);
+                    atomicMax(&b.err[1], cnt);
+                }
+            }
         }
     }
 }
@@ -386,7 +435,7 @@ cudaError_t launch_sortgather(const BoxDev& b, Launch l)
 
 cudaError_t launch_nlist(const BoxDev& b, Launch l)
 {
-    k_nlist<<<l.grid, LJ_CHUNK, 0, l.s>>>(b);
+    k_nlist<<<l.grid, LJ_LIST_THREADS, 0, l.s>>>(b);
     return cudaGetLastError();
 }
 

@@ -69,6 +69,7 @@ struct md_box {
     std::vector<RepDev> reps;
     std::vector<int4> chunks;
     std::vector<int4> tiles;
+    std::vector<int4> segs;
     // LJ
     bool lj_set = false;
     int nt = 1;
@@ -79,6 +80,7 @@ struct md_box {
     BoxDev d{};
     RepDev* d_rep = nullptr;
     int4* d_chunk = nullptr;
+    int4* d_seg = nullptr;
     LJDev* d_lj = nullptr;
     int4* d_tiles = nullptr;
     int* d_tile_sum = nullptr;
@@ -201,6 +203,8 @@ void invalidate_graphs(md_box* b)
 
 Launch lch(md_box* b) { return Launch{std::max(1, std::min((int)b->d.nchunk, b->nsm * 12)), LJ_CHUNK, b->stream}; }
 Launch lcell(md_box* b) { return Launch{std::max(1, std::min((b->d.ncell + 7) / 8, b->nsm * 8)), 256, b->stream}; }
+Launch lseg(md_box* b) { return Launch{std::max(1, std::min(b->d.nseg, b->nsm * 8)), LJ_SEG_THREADS, b->stream}; }
+Launch llist(md_box* b) { return Launch{std::max(1, std::min(b->d.nseg, b->nsm * 6)), LJ_LIST_THREADS, b->stream}; }
 
 // Fence: internal stream waits for the caller's stream.
 md_status enter(md_box* b)
@@ -262,17 +266,17 @@ md_status enqueue_rebuild(md_box* b, int from_abs)
     CK(b, launch_scan_tiles(b->d, b->d_tiles, (int)b->tiles.size(), b->d_tile_sum, lt));
     CK(b, launch_scatter(b->d, l));
     CK(b, launch_sortgather(b->d, lcell(b)));
-    CK(b, launch_nlist(b->d, l));
+    CK(b, launch_nlist(b->d, llist(b)));
     b->launches += 6;
     return MD_OK;
 }
 
 md_status enqueue_force(md_box* b, int energy, double* thermo_out_dev)
 {
-    CK(b, launch_force(b->d, energy, lch(b)));
+    CK(b, launch_force(b->d, energy, lseg(b)));
     b->launches += 1;
     if (energy && thermo_out_dev) {
-        Launch lt{std::max(1, std::min((b->nrep + 3) / 4, b->nsm)), 128, b->stream};
+        Launch lt{std::max(1, std::min(b->nrep, b->nsm * 4)), 512, b->stream};
         CK(b, launch_thermo(b->d, thermo_out_dev, 0, lt));
         b->launches += 1;
     }
@@ -284,6 +288,7 @@ md_status set_all_rebuild(md_box* b)
     std::vector<int> ones(b->nrep, 1);
     CK(b, cudaMemcpyAsync(b->d.rebuild_req, ones.data(), sizeof(int) * b->nrep,
                           cudaMemcpyHostToDevice, b->stream));
+    CK(b, cudaMemcpyAsync(b->d.any_req, ones.data(), sizeof(int), cudaMemcpyHostToDevice, b->stream));
     CK(b, cudaStreamSynchronize(b->stream));   // `ones` is pageable and local
     return MD_OK;
 }
@@ -293,10 +298,47 @@ md_status alloc_lists(md_box* b, int K)
     if (b->d.nbr) dev_release(b, b->d.nbr);
     b->d.nbr = nullptr;
     b->d.K = K;
-    uint32_t* nb;
-    CKS(dev_alloc(b, &nb, (size_t)b->np * (size_t)K, false));
+    uint16_t* nb;
+    CKS(dev_alloc(b, &nb, (size_t)b->np * (size_t)K + 64, false));
     b->d.nbr = nb;
     invalidate_graphs(b);
+    return MD_OK;
+}
+
+// Segments: runs of S cells along x inside each cell row.  S is chosen so
+// that a tile (9 rows x (S + 2) cells) holds ~1400 particles on average,
+// well inside the 2048 a 16-bit list entry can address.
+md_status make_segments(md_box* b, bool shrink)
+{
+    b->segs.clear();
+    for (int r = 0; r < b->nrep; ++r) {
+        RepDev& R = b->reps[r];
+        if (shrink) {
+            R.S = std::max(1, R.S / 2);
+        } else {
+            double per_cell = R.ncell > 0 ? (double)R.n / R.ncell : 0.0;
+            int S = per_cell > 0 ? (int)std::floor(1400.0 / (9.0 * per_cell)) - 2 : R.nc[0];
+            R.S = std::max(1, std::min(std::min(S, R.nc[0]), LJ_SEG_MAX_CELLS));
+        }
+        R.seg_off = (int)b->segs.size();
+        for (int row = 0; row < R.nc[1] * R.nc[2]; ++row)
+            for (int x0 = 0; x0 < R.nc[0]; x0 += R.S)
+                b->segs.push_back(make_int4(r, x0, row, std::min(R.S, R.nc[0] - x0)));
+        R.nseg = (int)b->segs.size() - R.seg_off;
+    }
+    BoxDev& d = b->d;
+    d.nseg = (int)b->segs.size();
+    invalidate_graphs(b);
+    dev_release(b, b->d_seg);
+    dev_release(b, d.part_f);
+    CKS(dev_alloc(b, &b->d_seg, b->segs.size(), false));
+    CKS(dev_alloc(b, &d.part_f, 2 * b->segs.size()));
+    d.seg = b->d_seg;
+    CK(b, cudaMemcpyAsync(b->d_seg, b->segs.data(), sizeof(int4) * b->segs.size(),
+                          cudaMemcpyHostToDevice, b->stream));
+    CK(b, cudaMemcpyAsync(b->d_rep, b->reps.data(), sizeof(RepDev) * b->reps.size(),
+                          cudaMemcpyHostToDevice, b->stream));
+    CK(b, cudaStreamSynchronize(b->stream));
     return MD_OK;
 }
 
@@ -304,13 +346,18 @@ md_status alloc_lists(md_box* b, int K)
 // then recompute the forces.
 md_status full_rebuild(md_box* b)
 {
-    for (int attempt = 0; attempt < 8; ++attempt) {
+    for (int attempt = 0; attempt < 24; ++attempt) {
         CKS(clear_err(b));
         CKS(set_all_rebuild(b));
         CKS(enqueue_rebuild(b, b->fresh_abs ? 1 : 0));
         int e2[2];
         CKS(read_err(b, e2));
         b->binned = true;
+        if (e2[0] & LJ_ERRBIT_TIMEOUT) return fail(b, MD_ERR_TIMEOUT, "list build: device wait timed out");
+        if (e2[0] & LJ_ERRBIT_TILE) {
+            CKS(make_segments(b, true));
+            continue;
+        }
         if (e2[0] & LJ_ERRBIT_CAPACITY) {
             // binning and sorting completed (xabs still holds the exact
             // positions, now in sorted slots); only the lists were cut short
@@ -366,13 +413,14 @@ md_status snapshot(md_box* b, bool restore)
 md_status enqueue_steps(md_box* b, int64_t n, double dt, int energy, double* ring, GraphEnt* ge)
 {
     Launch l = lch(b);
-    Launch lt{std::max(1, std::min((b->nrep + 3) / 4, b->nsm)), 128, b->stream};
+    Launch lt{std::max(1, std::min(b->nrep, b->nsm * 4)), 512, b->stream};
     size_t rs = (size_t)b->nrep * 4;
     auto mark = [&](int64_t s, int ph, int end) -> cudaError_t {
         if (!ge) return cudaSuccess;
         size_t k = (size_t)(s * 4 + ph);
         ge->used[k] = 1;
-        return cudaEventRecord(ge->ev[2 * k + end], b->stream);
+        // an external record becomes an event-record node of the graph
+        return cudaEventRecordWithFlags(ge->ev[2 * k + end], b->stream, cudaEventRecordExternal);
     };
     for (int64_t s = 0; s <= n; ++s) {
         int mode = s == 0 ? LJ_STEP_FIRST : (s == n ? LJ_STEP_LAST : LJ_STEP_MID);
@@ -391,7 +439,7 @@ md_status enqueue_steps(md_box* b, int64_t n, double dt, int energy, double* rin
         CKS(enqueue_rebuild(b, 0));
         CK(b, mark(s, 1, 1));
         CK(b, mark(s, 2, 0));
-        CK(b, launch_force(b->d, energy, l));
+        CK(b, launch_force(b->d, energy, lseg(b)));
         CK(b, mark(s, 2, 1));
         b->launches += 1;
     }
@@ -566,9 +614,9 @@ md_status md_batch_create(md_box** out, int32_t nrep, const int64_t* n, const do
         CKS(dev_alloc(b, &d.nbr_count, b->np));
         CKS(dev_alloc(b, &d.disp_max, nrep));
         CKS(dev_alloc(b, &d.rebuild_req, nrep));
+        CKS(dev_alloc(b, &d.any_req, 1));
         CKS(dev_alloc(b, &d.nbuild, nrep));
         CKS(dev_alloc(b, &d.err, 2));
-        CKS(dev_alloc(b, &d.part_f, 2 * std::max<size_t>(1, b->chunks.size())));
         CKS(dev_alloc(b, &d.part_k, std::max<size_t>(1, b->chunks.size())));
         CKS(dev_alloc(b, &b->d_type_user, std::max<int64_t>(1, ntot)));
         CK(b, cudaMemcpyAsync(b->d_rep, b->reps.data(), sizeof(RepDev) * b->reps.size(),
@@ -665,6 +713,11 @@ md_status md_set_lj(md_box* b, int32_t ntypes, const double* eps, const double* 
         double rc2 = rcut[k] * rcut[k];
         double c6 = (s2 / rc2) * (s2 / rc2) * (s2 / rc2);
         double sh = energy_shift ? 4.0 * eps[k] * (c6 * c6 - c6) : 0.0;
+        double s6 = s2 * s2 * s2;
+        h.c12[k] = (float)(48.0 * eps[k] * s6 * s6);
+        h.c6[k] = (float)(24.0 * eps[k] * s6);
+        h.e12[k] = (float)(4.0 * eps[k] * s6 * s6);
+        h.e6[k] = (float)(4.0 * eps[k] * s6);
         h.sig2[k] = (float)s2;
         h.eps48[k] = (float)(48.0 * eps[k]);
         h.eps4[k] = (float)(4.0 * eps[k]);
@@ -740,10 +793,11 @@ md_status md_set_lj(md_box* b, int32_t ntypes, const double* eps, const double* 
         CKS(dev_alloc(b, &b->d_tile_sum, b->tiles.size()));
         CK(b, cudaMemcpyAsync(b->d_tiles, b->tiles.data(), sizeof(int4) * b->tiles.size(),
                               cudaMemcpyHostToDevice, b->stream));
+        CKS(make_segments(b, false));
         // list capacity: expected neighbours at the densest replica, +30 %
         double expect = maxdens * 4.18879020478639 * rl * rl * rl;
         int K = round_up((int64_t)(1.3 * expect) + 16, 8);
-        if (b->min_capacity > 0) K = b->min_capacity;
+        if (b->min_capacity > 0) K = round_up(b->min_capacity, 8);
         CKS(alloc_lists(b, K));
     }
     b->lj_set = true;
@@ -799,6 +853,7 @@ md_status md_force(md_box* b, double* force_out, double* epot, double* virial)
         if (epot) epot[r] = th[4 * r + 0];
         if (virial) virial[r] = th[4 * r + 2];
     }
+    if (e2[0] & LJ_ERRBIT_TIMEOUT) return fail(b, MD_ERR_TIMEOUT, "md_force: a device-side wait timed out");
     if (e2[0] & LJ_ERRBIT_NONFINITE) return fail(b, MD_ERR_NONFINITE, "md_force: non-finite force");
     return MD_OK;
 }
@@ -837,13 +892,20 @@ md_status md_integrate(md_box* b, double dt, int64_t nsteps, int32_t ckpt_every,
                         b->prof_n[k % 4] += 1;
                     }
             }
-        if (e2[0] & LJ_ERRBIT_CAPACITY) {
+        if (e2[0] & (LJ_ERRBIT_CAPACITY | LJ_ERRBIT_TILE)) {
             if (++retries > 8) return fail(b, MD_ERR_CAPACITY, "md_integrate: list keeps overflowing");
             CKS(snapshot(b, true));
-            int K = round_up((int64_t)(e2[1] * 1.15) + 8, 8);
-            CKS(alloc_lists(b, std::max(K, b->d.K + 8)));
+            if (e2[0] & LJ_ERRBIT_TILE) CKS(make_segments(b, true));
+            if (e2[0] & LJ_ERRBIT_CAPACITY) {
+                int K = round_up((int64_t)(e2[1] * 1.15) + 8, 8);
+                CKS(alloc_lists(b, std::max(K, b->d.K + 8)));
+            }
             CKS(full_rebuild(b));
             continue;
+        }
+        if (e2[0] & LJ_ERRBIT_TIMEOUT) {
+            CKS(leave(b));
+            return fail(b, MD_ERR_TIMEOUT, "md_integrate: a device-side wait timed out");
         }
         if (e2[0] & LJ_ERRBIT_NONFINITE) {
             CKS(leave(b));
@@ -933,7 +995,7 @@ md_status md_get_nlist(md_box* b, int32_t* count, int64_t* nbr, int64_t cap, dou
     long long* tn = nbr ? reinterpret_cast<long long*>(st + ((cb + 255) & ~(size_t)255)) : nullptr;
     double* tp = pos ? reinterpret_cast<double*>(st + ((cb + 255) & ~(size_t)255) + ((nb + 255) & ~(size_t)255))
                      : nullptr;
-    CK(b, launch_get_nlist(b->d, tc, tn, (long long)cap, tp, lch(b)));
+    CK(b, launch_get_nlist(b->d, tc, tn, (long long)cap, tp, lseg(b)));
     std::vector<int> hc(b->ntot);
     CK(b, cudaMemcpyAsync(hc.data(), tc, cb, cudaMemcpyDeviceToHost, b->stream));
     if (nbr) CK(b, cudaMemcpyAsync(nbr, tn, nb, is_device_ptr(nbr) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, b->stream));
@@ -1015,7 +1077,7 @@ md_status md_set_tuning(md_box* b, int32_t block_force, int32_t block_list, int3
     if (capacity > 0 && b->lj_set) {
         // re-layout the lists at this capacity now (they regrow on overflow)
         CKS(enter(b));
-        CKS(alloc_lists(b, round_up(capacity, 1)));
+        CKS(alloc_lists(b, round_up(capacity, 8)));   // 16-byte list rows
         CKS(full_rebuild(b));
         CKS(leave(b));
     }

@@ -10,26 +10,40 @@
 //     MD_PREC_MIXED_DS the offsets and velocities are double-single pairs
 //     (hi, lo) of FP32; otherwise FP64.
 //   * posq[p] = (float offset x, y, z, type bits) feeds the FP32 pair kernels.
-//   * Verlet lists (Sec. 3) are 32-bit entries (stencil code << 27 | j) in a
-//     warp-blocked layout: entry s of particle p lives at
-//     nbr[(p >> 5) * K * 32 + s * 32 + (p & 31)], so the 32 lists of a warp
-//     are one contiguous K*128-byte block and each slot load is coalesced.
-//     The stencil code k = 9(dz+1) + 3(dy+1) + (dx+1) names the image shift
-//     of j's cell relative to i's cell, so d_ij = (o_i - o_j) - k_shift.
+//   * pair work is done per "segment": a run of up to S consecutive cells
+//     along x inside one row (cy, cz) of a replica.  Its particles are one
+//     contiguous slot range, and the 27-cell neighbourhood of all its cells
+//     is the "tile": 9 rows x (S + 2) cells, i.e. at most 18 contiguous slot
+//     ranges ("pieces"), staged in shared memory.
+//   * Verlet lists (Sec. 3) are 16-bit entries (stencil code << 11 | tile
+//     index), so a tile holds at most 2048 particles.  The stencil code
+//     k = 9(dz+1) + 3(dy+1) + (dx+1) names the image shift of j's cell
+//     relative to i's cell, so d_ij = (o_i - o_j) - shift(k).  Entry s of
+//     particle p is nbr[p K + s] (K a multiple of 8): each thread streams its
+//     own list in 16-byte groups of 8 entries, several groups in flight.
 #pragma once
 
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #define LJ_MAXT 8
-#define LJ_IDX_BITS 27
-#define LJ_IDX_MASK ((1u << LJ_IDX_BITS) - 1u)
+#define LJ_IDX_BITS 27         // slot indices must stay below 2^27
+#define LJ_TILE_BITS 11
+#define LJ_TILE_MAX (1 << LJ_TILE_BITS)
+#define LJ_TILE_MASK (LJ_TILE_MAX - 1)
 #define LJ_CHUNK 128           // particles per work item (one CTA pass)
+#define LJ_SEG_THREADS 256     // threads of the segment pair kernels
+#define LJ_LIST_THREADS 256    // threads of the list-build kernel
+#define LJ_F64_THREADS 128     // threads of the FP64 pair kernel (one per particle)
+#define LJ_TPP 8               // threads per particle in the pair kernels
+#define LJ_SEG_MAX_CELLS 16    // most cells in one segment
+#define LJ_LIST_SMEM (32 * 1024)   // bytes of a segment's list staged in smem
 
 // error word bits (err[0]); err[1] = largest list length seen
 #define LJ_ERRBIT_CAPACITY 1
 #define LJ_ERRBIT_NONFINITE 2
 #define LJ_ERRBIT_TIMEOUT 4
+#define LJ_ERRBIT_TILE 8       // a tile exceeded LJ_TILE_MAX particles
 
 // integrate kernel modes
 #define LJ_STEP_FIRST 0        // half kick + drift
@@ -45,14 +59,27 @@ struct RepDev {
     int cell_off, ncell;
     int p_off, n;              // first slot, real particles
     int u_off;                 // first user index
-    int chunk_off, nchunk;     // work items of this replica
-    int pad;
+    int chunk_off, nchunk;     // particle work items of this replica
+    int seg_off, nseg;         // segments of this replica
+    int S;                     // cells per segment (along x)
+};
+
+// Slot ranges of a segment's tile: piece q (0..17) is row rr = q/2 with
+// rr = 3(dz+1) + (dy+1); tile index of slot j in piece q = base[q] + j - beg[q].
+struct Tile {
+    int beg[18];
+    int end[18];
+    int base[18];
+    int total;
+    int p0, n;                 // the segment's own particles
 };
 
 // pair parameters, FP32 and FP64 copies: per type pair (a*nt+b)
 struct LJDev {
     int nt;
     int shift_on;
+    // FP32 lj1/lj2 form: f = r2i r6i (c12 r6i - c6), u = r6i (e12 r6i - e6) - shift
+    float c12[LJ_MAXT * LJ_MAXT], c6[LJ_MAXT * LJ_MAXT], e12[LJ_MAXT * LJ_MAXT], e6[LJ_MAXT * LJ_MAXT];
     float sig2[LJ_MAXT * LJ_MAXT], eps48[LJ_MAXT * LJ_MAXT], eps4[LJ_MAXT * LJ_MAXT];
     float rc2[LJ_MAXT * LJ_MAXT], shift[LJ_MAXT * LJ_MAXT];
     double dsig2[LJ_MAXT * LJ_MAXT], deps48[LJ_MAXT * LJ_MAXT], deps4[LJ_MAXT * LJ_MAXT];
@@ -72,6 +99,8 @@ struct BoxDev {
     double rl2;
     const RepDev* rep;
     const int4* chunk;         // (rep, p_begin, p_end, chunk index)
+    const int4* seg;           // (rep, first cell x, row = cy + ny cz, cells)
+    int nseg;
     const LJDev* lj;
     // particle arrays (sorted order)
     float4* posq;
@@ -99,15 +128,16 @@ struct BoxDev {
     int* cell_end;
     const int* cell_rep;
     // lists
-    uint32_t* nbr;
+    uint16_t* nbr;
     int* nbr_count;
     // per-replica control
     unsigned* disp_max;        // FP32 bits of the largest |displacement|^2
     int* rebuild_req;          // host-forced rebuild
+    int* any_req;              // nonzero when some replica may need a build
     unsigned long long* nbuild;
     int* err;
     // per-chunk FP64 partial sums
-    double* part_f;            // [chunk*2 + 0] = E_pot share, [+1] = W share
+    double* part_f;            // [seg*2 + 0] = E_pot share, [+1] = W share
     double* part_k;            // [chunk] = E_kin share
 };
 
@@ -155,9 +185,133 @@ __device__ __forceinline__ void ds_from_double(double x, float& h, float& l)
     l = __double2float_rn(x - (double)h);
 }
 
+// Cheap block-level early exit of the rebuild kernels: nothing to do unless
+// the integrator or the host raised the box-wide request word.
+__device__ __forceinline__ bool box_needs_rebuild(const BoxDev& b)
+{
+    return *((volatile const int*)b.any_req) != 0;
+}
+
 __device__ __forceinline__ bool rep_needs_rebuild(const BoxDev& b, int r)
 {
     return b.rebuild_req[r] != 0 || __uint_as_float(b.disp_max[r]) > b.disp_thr2;
+}
+
+__device__ __forceinline__ int wrapi(int x, int n) { return x < 0 ? x + n : (x >= n ? x - n : x); }
+
+// ---- bulk asynchronous copies (TMA, non-tensor) into shared memory ----
+// One thread arms an mbarrier with the byte count and issues one
+// cp.async.bulk per contiguous piece; every thread then waits on the
+// barrier's phase.  Addresses and sizes are multiples of 16 bytes.
+__device__ __forceinline__ unsigned smem_u32(const void* p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arm(unsigned long long* bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+// Order earlier generic-proxy accesses of shared memory before later
+// async-proxy (bulk copy) writes to it.
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// Wait for phase `parity` of the barrier; gives up after a bounded number of
+// polls (returns false; the caller records LJ_ERRBIT_TIMEOUT and stops).
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity)
+{
+    unsigned a = smem_u32(bar);
+    for (int it = 0; it < (1 << 24); ++it) {
+        unsigned ok;
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// Stage the FP32 offsets of a tile (and, if list_bytes > 0, a contiguous
+// list block) into shared memory with bulk copies
+// (thread 0 issues; all threads wait).  Returns false, for every thread of
+// the block alike, on a timed-out wait.  Must be called by all threads.
+__device__ __forceinline__ bool stage_tile_bulk(const float4* posq, const Tile& t, float4* s_tile,
+                                                unsigned long long* bar, unsigned& phase, int* err,
+                                                void* s_list = nullptr, const void* g_list = nullptr,
+                                                unsigned list_bytes = 0)
+{
+    if (threadIdx.x == 0) {
+        fence_proxy_async_smem();
+        unsigned bytes = (unsigned)t.total * 16u + list_bytes;
+        mbar_arm(bar, bytes);
+        for (int q = 0; q < 18; ++q) {
+            int len = t.end[q] - t.beg[q];
+            if (len > 0) bulk_g2s(s_tile + t.base[q], posq + t.beg[q], (unsigned)len * 16u, bar);
+        }
+        if (list_bytes) bulk_g2s(s_list, g_list, list_bytes, bar);
+    }
+    bool ok = mbar_wait(bar, phase);
+    phase ^= 1u;
+    ok = __syncthreads_and(ok) != 0;   // one decision for the whole block
+    if (!ok && threadIdx.x == 0) atomicOr(err, LJ_ERRBIT_TIMEOUT);
+    return ok;
+}
+
+// Slot ranges of segment sg's tile (any thread may compute it).
+__device__ __forceinline__ void seg_tile(const BoxDev& b, const RepDev& R, int4 sg, Tile& t)
+{
+    const int nx = R.nc[0], ny = R.nc[1], nz = R.nc[2];
+    const int cx0 = sg.y, cy = sg.z % ny, cz = sg.z / ny, S = sg.w;
+    int acc = 0;
+    for (int rr = 0; rr < 9; ++rr) {
+        int dy = rr % 3 - 1, dz = rr / 3 - 1;
+        int rowc = R.cell_off + nx * (wrapi(cy + dy, ny) + ny * wrapi(cz + dz, nz));
+        int a0, a1, b0 = 0, b1 = -1;   // cell x ranges of the two pieces (inclusive)
+        if (S + 2 >= nx) {
+            a0 = 0;
+            a1 = nx - 1;
+        } else if (cx0 - 1 < 0) {
+            a0 = nx - 1; a1 = nx - 1; b0 = 0; b1 = cx0 + S;
+        } else if (cx0 + S >= nx) {
+            a0 = cx0 - 1; a1 = nx - 1; b0 = 0; b1 = cx0 + S - nx;
+        } else {
+            a0 = cx0 - 1; a1 = cx0 + S;
+        }
+        int q = 2 * rr;
+        t.beg[q] = b.cell_start[rowc + a0];
+        t.end[q] = b.cell_end[rowc + a1];
+        t.base[q] = acc;
+        acc += t.end[q] - t.beg[q];
+        if (b1 >= b0) {
+            t.beg[q + 1] = b.cell_start[rowc + b0];
+            t.end[q + 1] = b.cell_end[rowc + b1];
+        } else {
+            t.beg[q + 1] = t.end[q + 1] = 0;
+        }
+        t.base[q + 1] = acc;
+        acc += t.end[q + 1] - t.beg[q + 1];
+    }
+    t.total = acc;
+    int c0 = R.cell_off + cx0 + nx * sg.z;
+    t.p0 = b.cell_start[c0];
+    t.n = b.cell_end[c0 + S - 1] - t.p0;
 }
 
 // ---- launchers (defined in the kernel translation units) ----
