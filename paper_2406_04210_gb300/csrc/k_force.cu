@@ -42,41 +42,18 @@ __device__ __forceinline__ void block_sum2(double& a, double& c, double (*s)[32]
     __syncthreads();
 }
 
-// Per-segment prologue shared by the pair kernels: tile ranges, image-shift
-// table of the replica, and (first segment of a replica) the reset of the
-// rebuild triggers, which the list update of this step has consumed.
-__device__ __forceinline__ void seg_prologue(const BoxDev& b, int w, int4 sg, const RepDev& R,
-                                             Tile& t, float4* s_shift, int& cur_r, bool reset)
-{
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        seg_tile(b, R, sg, t);
-        if (reset && w == 0) *b.any_req = 0;   // the list update has run
-        if (reset && w == R.seg_off) {
-            b.disp_max[sg.x] = 0u;
-            b.rebuild_req[sg.x] = 0;
-        }
-    }
-    if (sg.x != cur_r && threadIdx.x < 27) {
-        int k = threadIdx.x;
-        s_shift[k] = make_float4((float)(k % 3 - 1) * R.ellf[0], (float)((k / 3) % 3 - 1) * R.ellf[1],
-                                 (float)(k / 9 - 1) * R.ellf[2], 0.f);
-    }
-    cur_r = sg.x;
-    __syncthreads();
-}
-
 // One pair term of the FP32 force: accumulates f d into (fx, fy, fz) and,
 // with ENERGY, the pair energy and virial; the term is masked (not branched)
-// by the cutoff test, so threads of a particle never diverge.
+// by the cutoff test, so the threads of a particle never diverge.
 template <bool MONO, bool ENERGY>
-__device__ __forceinline__ void pair_f32(unsigned ent, const float4& pi, int ti, const float4* s_tile,
+__device__ __forceinline__ void pair_f32(unsigned ent, bool valid, const float4& pi, int ti,
+                                         const float4* __restrict__ posq,
                                          const float4* s_shift, const float4* s_lj, const float* s_rc2,
                                          const float* s_esh, int nt, const float4& mlj, float mrc2,
                                          float mesh, float& fx, float& fy, float& fz, float& e, float& vir)
 {
-    const float4 pj = s_tile[ent & LJ_TILE_MASK];
-    const float4 sh = s_shift[ent >> LJ_TILE_BITS];
+    const float4 pj = __ldg(posq + (ent & LJ_IDX_MASK));
+    const float4 sh = s_shift[ent >> LJ_IDX_BITS];
     const float dx = (pi.x - pj.x) - sh.x;
     const float dy = (pi.y - pj.y) - sh.y;
     const float dz = (pi.z - pj.z) - sh.z;
@@ -95,8 +72,9 @@ __device__ __forceinline__ void pair_f32(unsigned ent, const float4& pi, int ti,
     }
     const float r2i = __fdividef(1.0f, r2);
     const float r6i = r2i * r2i * r2i;
-    float f = r2i * r6i * fmaf(c.x, r6i, -c.y);   // c = (48 eps s^12, 24 eps s^6, 4 eps s^12, 4 eps s^6)
-    const bool in = r2 < rc2;
+    // c = (48 eps sigma^12, 24 eps sigma^6, 4 eps sigma^12, 4 eps sigma^6)
+    float f = r2i * r6i * fmaf(c.x, r6i, -c.y);
+    const bool in = valid && r2 < rc2;
     f = in ? f : 0.f;
     fx = fmaf(f, dx, fx);
     fy = fmaf(f, dy, fy);
@@ -108,67 +86,15 @@ __device__ __forceinline__ void pair_f32(unsigned ent, const float4& pi, int ti,
     }
 }
 
-// FP32 pair force over one segment per block, LJ_TPP threads per particle.
-// The tile's FP32 offsets and the segment's list block (rows of K entries of
-// its particles, contiguous) are staged in shared memory by bulk copies; the
-// 8 threads of a particle take entries s, s+8, ... of its list (two at a time
-// for instruction-level parallelism) and combine their partial forces with
-// shuffles.  MONO: a single species, parameters in registers.
-template <bool MONO, bool ENERGY, bool LSM>
-__device__ __forceinline__ void force_segment_f32(const BoxDev& b, int n, int p0, const float4* s_tile,
-                                                  const uint16_t* s_list, const float4* s_shift,
-                                                  const float4* s_lj, const float* s_rc2, const float* s_esh,
-                                                  int nt, const float4& mlj, float mrc2, float mesh, float& e,
-                                                  float& vir)
-{
-    const int K = b.K;
-    const int grp = threadIdx.x / LJ_TPP, l8 = threadIdx.x % LJ_TPP;
-    for (int base = 0; base < n; base += LJ_SEG_THREADS / LJ_TPP) {
-        const int il = base + grp;
-        const bool act = il < n;
-        const int p = p0 + il;
-        float4 pi = make_float4(0.f, 0.f, 0.f, 0.f);
-        int cnt = 0;
-        if (act) {
-            pi = b.posq[p];
-            cnt = min(b.nbr_count[p], K);
-        }
-        const int ti = __float_as_int(pi.w);
-        const uint16_t* L = LSM ? s_list + (size_t)il * K : b.nbr + (size_t)K * p;
-        float fx = 0.f, fy = 0.f, fz = 0.f, fx2 = 0.f, fy2 = 0.f, fz2 = 0.f;
-        int s = l8;
-        for (; s + LJ_TPP < cnt; s += 2 * LJ_TPP) {
-            const unsigned e0 = L[s], e1 = L[s + LJ_TPP];
-            pair_f32<MONO, ENERGY>(e0, pi, ti, s_tile, s_shift, s_lj, s_rc2, s_esh, nt, mlj, mrc2, mesh, fx, fy, fz, e, vir);
-            pair_f32<MONO, ENERGY>(e1, pi, ti, s_tile, s_shift, s_lj, s_rc2, s_esh, nt, mlj, mrc2, mesh, fx2, fy2, fz2, e, vir);
-        }
-        if (s < cnt)
-            pair_f32<MONO, ENERGY>(L[s], pi, ti, s_tile, s_shift, s_lj, s_rc2, s_esh, nt, mlj, mrc2, mesh, fx, fy, fz, e, vir);
-        fx += fx2;
-        fy += fy2;
-        fz += fz2;
-#pragma unroll
-        for (int o = LJ_TPP / 2; o > 0; o >>= 1) {
-            fx += __shfl_xor_sync(0xffffffffu, fx, o);
-            fy += __shfl_xor_sync(0xffffffffu, fy, o);
-            fz += __shfl_xor_sync(0xffffffffu, fz, o);
-        }
-        if (act && l8 == 0) {
-            b.force4[p] = make_float4(fx, fy, fz, 0.f);
-            if (!isfinite(fx + fy + fz)) atomicOr(&b.err[0], LJ_ERRBIT_NONFINITE);
-        }
-    }
-}
-
+// FP32 pair force (Sec. 4/5), one 128-particle chunk per block pass, LJ_TPP
+// threads per particle.  The 8 threads of a particle take entries s, s+8,
+// ... of its list (two at a time for instruction-level parallelism), gather
+// the neighbours' FP32 offsets through L1 and combine their partial forces
+// with shuffles.  MONO: a single species, parameters in registers.
 template <bool MONO, bool ENERGY>
-__global__ void __launch_bounds__(LJ_SEG_THREADS, 3) k_force_f32(BoxDev b)
+__global__ void __launch_bounds__(LJ_FORCE_THREADS) k_force_f32(BoxDev b)
 {
-    extern __shared__ __align__(16) unsigned char dsm[];
-    float4* s_tile = reinterpret_cast<float4*>(dsm);
-    uint16_t* s_list = reinterpret_cast<uint16_t*>(dsm + LJ_TILE_MAX * 16);
     __shared__ float4 s_shift[32];
-    __shared__ Tile s_t;
-    __shared__ __align__(8) unsigned long long s_bar;
     __shared__ float4 s_lj[LJ_MAXT * LJ_MAXT];   // c12, c6, e12, e6
     __shared__ float s_rc2[LJ_MAXT * LJ_MAXT];
     __shared__ float s_esh[LJ_MAXT * LJ_MAXT];
@@ -180,34 +106,89 @@ __global__ void __launch_bounds__(LJ_SEG_THREADS, 3) k_force_f32(BoxDev b)
         s_rc2[k] = lj->rc2[k];
         s_esh[k] = lj->shift[k];
     }
-    if (threadIdx.x >= 27 && threadIdx.x < 32) s_shift[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
     const float4 mlj = make_float4(lj->c12[0], lj->c6[0], lj->e12[0], lj->e6[0]);
     const float mrc2 = lj->rc2[0];
     const float mesh = lj->shift[0];
-    if (threadIdx.x == 0) mbar_init(&s_bar, 1);
-    unsigned phase = 0;
-    int cur_r = -1;
     const int K = b.K;
-    for (int w = blockIdx.x; w < b.nseg; w += gridDim.x) {
-        int4 sg = b.seg[w];
-        const RepDev& R = b.rep[sg.x];
-        seg_prologue(b, w, sg, R, s_t, s_shift, cur_r, true);
-        const int n = s_t.n, p0 = s_t.p0;
-        const bool ok = s_t.total <= LJ_TILE_MAX;   // else flagged by k_nlist
-        const unsigned list_bytes = (unsigned)n * (unsigned)K * 2u;
-        const bool lsm = ok && list_bytes <= LJ_LIST_SMEM;
-        if (ok && s_t.total + n > 0 &&
-            !stage_tile_bulk(b.posq, s_t, s_tile, &s_bar, phase, b.err, s_list,
-                             b.nbr + (size_t)K * p0, lsm ? list_bytes : 0u))
-            return;
+    const int grp = threadIdx.x / LJ_TPP, l8 = threadIdx.x % LJ_TPP;
+    const float4* __restrict__ posq = b.posq;
+    int cur_r = -1;
+    for (int w = blockIdx.x; w < b.nchunk; w += gridDim.x) {
+        const int4 ch = b.chunk[w];
+        const int r = ch.x;
+        if (r != cur_r) {                       // block-uniform
+            __syncthreads();
+            if (threadIdx.x < 32) {
+                const RepDev& R = b.rep[r];
+                const int k = threadIdx.x;
+                s_shift[k] = k < 27 ? make_float4((float)(k % 3 - 1) * R.ellf[0], (float)((k / 3) % 3 - 1) * R.ellf[1],
+                                                  (float)(k / 9 - 1) * R.ellf[2], 0.f)
+                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            __syncthreads();
+            cur_r = r;
+        }
+        if (threadIdx.x == 0) {
+            if (w == 0) *b.any_req = 0;         // the list update of this step has run
+            if (w == b.rep[r].chunk_off) {      // clear the replica's rebuild triggers
+                b.disp_max[r] = 0u;
+                b.rebuild_req[r] = 0;
+            }
+        }
         float e = 0.f, vir = 0.f;
-        if (ok) {
-            if (lsm)
-                force_segment_f32<MONO, ENERGY, true>(b, n, p0, s_tile, s_list, s_shift, s_lj, s_rc2, s_esh, nt,
-                                                      mlj, mrc2, mesh, e, vir);
-            else
-                force_segment_f32<MONO, ENERGY, false>(b, n, p0, s_tile, s_list, s_shift, s_lj, s_rc2, s_esh, nt,
-                                                       mlj, mrc2, mesh, e, vir);
+        for (int base = ch.y; base < ch.z; base += LJ_FORCE_THREADS / LJ_TPP) {
+            const int p = base + grp;
+            const bool act = p < ch.z;
+            float4 pi = make_float4(0.f, 0.f, 0.f, 0.f);
+            int cnt = 0;
+            if (act) {
+                pi = posq[p];
+                cnt = min(b.nbr_count[p], K);
+            }
+            const int ti = __float_as_int(pi.w);
+            const uint32_t* L = b.nbr + (size_t)K * p;
+            // lane l8 takes entries l8 + 8i; a block of 8 of them (64 entries
+            // of the particle) is loaded at once and the next block is in
+            // flight while this one is computed
+            const unsigned self = (13u << LJ_IDX_BITS) | (unsigned)(act ? p : 0);
+            unsigned cur[8], nxt[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int s = l8 + LJ_TPP * i;
+                cur[i] = s < cnt ? __ldcs(L + s) : self;
+            }
+            float fx = 0.f, fy = 0.f, fz = 0.f, fx2 = 0.f, fy2 = 0.f, fz2 = 0.f;
+            for (int blk = 0; blk * 8 * LJ_TPP < cnt; ++blk) {
+                const int nb = (blk + 1) * 8 * LJ_TPP;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int s = nb + l8 + LJ_TPP * i;
+                    nxt[i] = s < cnt ? __ldcs(L + s) : self;
+                }
+#pragma unroll
+                for (int i = 0; i < 8; i += 2) {
+                    const int s = blk * 8 * LJ_TPP + l8 + LJ_TPP * i;
+                    pair_f32<MONO, ENERGY>(cur[i], s < cnt, pi, ti, posq, s_shift, s_lj, s_rc2, s_esh, nt, mlj,
+                                           mrc2, mesh, fx, fy, fz, e, vir);
+                    pair_f32<MONO, ENERGY>(cur[i + 1], s + LJ_TPP < cnt, pi, ti, posq, s_shift, s_lj, s_rc2,
+                                           s_esh, nt, mlj, mrc2, mesh, fx2, fy2, fz2, e, vir);
+                }
+#pragma unroll
+                for (int i = 0; i < 8; ++i) cur[i] = nxt[i];
+            }
+            fx += fx2;
+            fy += fy2;
+            fz += fz2;
+#pragma unroll
+            for (int o = LJ_TPP / 2; o > 0; o >>= 1) {
+                fx += __shfl_xor_sync(0xffffffffu, fx, o);
+                fy += __shfl_xor_sync(0xffffffffu, fy, o);
+                fz += __shfl_xor_sync(0xffffffffu, fz, o);
+            }
+            if (act && l8 == 0) {
+                b.force4[p] = make_float4(fx, fy, fz, 0.f);
+                if (!isfinite(fx + fy + fz)) atomicOr(&b.err[0], LJ_ERRBIT_NONFINITE);
+            }
         }
         if (ENERGY) {
             double de = 0.5 * (double)e, dw = 0.5 * (double)vir;
@@ -220,52 +201,51 @@ __global__ void __launch_bounds__(LJ_SEG_THREADS, 3) k_force_f32(BoxDev b)
     }
 }
 
-// FP64 pair force (MD_PREC_FP64): same lists; the tile holds slot indices
-// and the FP64 offsets are read from global memory.
+// FP64 pair force (MD_PREC_FP64), one thread per particle over 128-particle
+// chunks, FP64 cell-relative offsets gathered from global memory.
 template <bool ENERGY>
 __global__ void __launch_bounds__(LJ_F64_THREADS) k_force_f64(BoxDev b)
 {
-    __shared__ int s_slot[LJ_TILE_MAX];
-    __shared__ float4 s_shift[27];
     __shared__ double s_sh[3][27];
-    __shared__ Tile s_t;
     __shared__ double s_red[2][32];
     const LJDev* lj = b.lj;
     const int nt = lj->nt;
     const int np = b.np;
     int cur_r = -1;
-    for (int w = blockIdx.x; w < b.nseg; w += gridDim.x) {
-        int4 sg = b.seg[w];
-        const RepDev& R = b.rep[sg.x];
-        int prev = cur_r;
-        seg_prologue(b, w, sg, R, s_t, s_shift, cur_r, true);
-        if (sg.x != prev && threadIdx.x < 27) {
-            int k = threadIdx.x;
-            s_sh[0][k] = (double)(k % 3 - 1) * R.ell[0];
-            s_sh[1][k] = (double)((k / 3) % 3 - 1) * R.ell[1];
-            s_sh[2][k] = (double)(k / 9 - 1) * R.ell[2];
+    for (int w = blockIdx.x; w < b.nchunk; w += gridDim.x) {
+        const int4 ch = b.chunk[w];
+        const int r = ch.x;
+        if (r != cur_r) {
+            __syncthreads();
+            if (threadIdx.x < 27) {
+                const RepDev& R = b.rep[r];
+                const int k = threadIdx.x;
+                s_sh[0][k] = (double)(k % 3 - 1) * R.ell[0];
+                s_sh[1][k] = (double)((k / 3) % 3 - 1) * R.ell[1];
+                s_sh[2][k] = (double)(k / 9 - 1) * R.ell[2];
+            }
+            __syncthreads();
+            cur_r = r;
         }
-        const int n = s_t.n, p0 = s_t.p0;
-        const bool ok = s_t.total <= LJ_TILE_MAX;
-        if (ok) {
-            for (int q = 0; q < 18; ++q) {
-                int beg = s_t.beg[q], len = s_t.end[q] - beg, base = s_t.base[q];
-                for (int t = threadIdx.x; t < len; t += blockDim.x) s_slot[base + t] = beg + t;
+        if (threadIdx.x == 0) {
+            if (w == 0) *b.any_req = 0;
+            if (w == b.rep[r].chunk_off) {
+                b.disp_max[r] = 0u;
+                b.rebuild_req[r] = 0;
             }
         }
-        __syncthreads();
+        const int p = ch.y + (int)threadIdx.x;
         double e = 0.0, vir = 0.0;
-        for (int il = threadIdx.x; il < n && ok; il += blockDim.x) {
-            int p = p0 + il;
+        if (p < ch.z) {
             double xi = b.off[p], yi = b.off[np + p], zi = b.off[2 * np + p];
             int ti = b.type[p];
             int cnt = min(b.nbr_count[p], b.K);
-            const uint16_t* lp = b.nbr + (size_t)b.K * p;
+            const uint32_t* lp = b.nbr + (size_t)b.K * p;
             double fx = 0.0, fy = 0.0, fz = 0.0;
             for (int s = 0; s < cnt; ++s) {
                 unsigned ent = __ldcs(lp + s);
-                int j = s_slot[ent & LJ_TILE_MASK];
-                int k = (int)(ent >> LJ_TILE_BITS);
+                int j = (int)(ent & LJ_IDX_MASK);
+                int k = (int)(ent >> LJ_IDX_BITS);
                 double dx = (xi - __ldg(&b.off[j])) - s_sh[0][k];
                 double dy = (yi - __ldg(&b.off[np + j])) - s_sh[1][k];
                 double dz = (zi - __ldg(&b.off[2 * np + j])) - s_sh[2][k];
@@ -310,7 +290,7 @@ __global__ void __launch_bounds__(512) k_thermo(BoxDev b, double* out, int with_
     for (int r = blockIdx.x; r < b.nrep; r += gridDim.x) {
         const RepDev& R = b.rep[r];
         double e = 0.0, w = 0.0, k = 0.0;
-        for (int c = R.seg_off + (int)threadIdx.x; c < R.seg_off + R.nseg; c += blockDim.x) {
+        for (int c = R.chunk_off + (int)threadIdx.x; c < R.chunk_off + R.nchunk; c += blockDim.x) {
             e += b.part_f[2 * c];
             w += b.part_f[2 * c + 1];
         }
@@ -344,30 +324,19 @@ __global__ void __launch_bounds__(512) k_thermo(BoxDev b, double* out, int with_
 
 }  // namespace
 
-template <bool MONO, bool ENERGY>
-static cudaError_t launch_f32(const BoxDev& b, Launch l)
-{
-    const int dyn = LJ_TILE_MAX * 16 + LJ_LIST_SMEM;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_force_f32<MONO, ENERGY>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
-    k_force_f32<MONO, ENERGY><<<l.grid, LJ_SEG_THREADS, dyn, l.s>>>(b);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_force(const BoxDev& b, int energy, Launch l)
 {
     if (b.prec == 2) {
         if (energy) k_force_f64<true><<<l.grid, LJ_F64_THREADS, 0, l.s>>>(b);
         else k_force_f64<false><<<l.grid, LJ_F64_THREADS, 0, l.s>>>(b);
-        return cudaGetLastError();
+    } else if (b.nt == 1) {
+        if (energy) k_force_f32<true, true><<<l.grid, LJ_FORCE_THREADS, 0, l.s>>>(b);
+        else k_force_f32<true, false><<<l.grid, LJ_FORCE_THREADS, 0, l.s>>>(b);
+    } else {
+        if (energy) k_force_f32<false, true><<<l.grid, LJ_FORCE_THREADS, 0, l.s>>>(b);
+        else k_force_f32<false, false><<<l.grid, LJ_FORCE_THREADS, 0, l.s>>>(b);
     }
-    if (b.nt == 1) return energy ? launch_f32<true, true>(b, l) : launch_f32<true, false>(b, l);
-    return energy ? launch_f32<false, true>(b, l) : launch_f32<false, false>(b, l);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_thermo(const BoxDev& b, double* out, int with_kin, Launch l)

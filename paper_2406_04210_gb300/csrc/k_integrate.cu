@@ -241,36 +241,24 @@ __global__ void __launch_bounds__(LJ_CHUNK) k_force_out(BoxDev b, double* f)
     }
 }
 
-__global__ void __launch_bounds__(LJ_SEG_THREADS) k_get_nlist(BoxDev b, int* count, long long* nbr,
-                                                              long long cap, double* pos)
+__global__ void __launch_bounds__(LJ_CHUNK) k_get_nlist(BoxDev b, int* count, long long* nbr,
+                                                        long long cap, double* pos)
 {
-    __shared__ Tile s_t;
     const int np = b.np;
-    for (int w = blockIdx.x; w < b.nseg; w += gridDim.x) {
-        int4 sg = b.seg[w];
-        __syncthreads();
-        if (threadIdx.x == 0) seg_tile(b, b.rep[sg.x], sg, s_t);
-        __syncthreads();
-        const int n = s_t.n, p0 = s_t.p0;
-        for (int il = threadIdx.x; il < n; il += blockDim.x) {
-            int p = p0 + il;
-            long long gu = b.uid[p];
-            int cnt = b.nbr_count[p];
-            count[gu] = cnt;
-            if (pos)
-                for (int c = 0; c < 3; ++c) pos[3 * gu + c] = b.xabs[c * np + p];
-            if (nbr && s_t.total <= LJ_TILE_MAX) {
-                int m = cnt < b.K ? cnt : b.K;
-                if ((long long)m > cap) m = (int)cap;
-                const uint16_t* lp = b.nbr + (size_t)b.K * p;
-                for (int s = 0; s < m; ++s) {
-                    int idx = lp[s] & LJ_TILE_MASK;
-                    int q = 0;
-                    while (q < 17 && idx >= s_t.base[q] + (s_t.end[q] - s_t.beg[q])) ++q;
-                    int j = s_t.beg[q] + (idx - s_t.base[q]);
-                    nbr[gu * cap + s] = b.uid[j];
-                }
-            }
+    for (int w = blockIdx.x; w < b.nchunk; w += gridDim.x) {
+        int4 ch = b.chunk[w];
+        int p = ch.y + (int)threadIdx.x;
+        if (p >= ch.z) continue;
+        long long gu = b.uid[p];
+        int cnt = b.nbr_count[p];
+        count[gu] = cnt;
+        if (pos)
+            for (int c = 0; c < 3; ++c) pos[3 * gu + c] = b.xabs[c * np + p];
+        if (nbr) {
+            int m = cnt < b.K ? cnt : b.K;
+            if ((long long)m > cap) m = (int)cap;
+            const uint32_t* lp = b.nbr + (size_t)b.K * p;
+            for (int s = 0; s < m; ++s) nbr[gu * cap + s] = b.uid[lp[s] & LJ_IDX_MASK];
         }
     }
 }
@@ -306,7 +294,7 @@ cudaError_t launch_force_out(const BoxDev& b, double* f, Launch l)
 cudaError_t launch_get_nlist(const BoxDev& b, int* count, long long* nbr, long long cap,
                              double* pos, Launch l)
 {
-    k_get_nlist<<<l.grid, LJ_SEG_THREADS, 0, l.s>>>(b, count, nbr, cap, pos);
+    k_get_nlist<<<l.grid, LJ_CHUNK, 0, l.s>>>(b, count, nbr, cap, pos);
     return cudaGetLastError();
 }
 

@@ -360,7 +360,7 @@ __global__ void __launch_bounds__(LJ_LIST_THREADS) k_nlist(BoxDev b)
             const int p = p0 + il;
             const float4 pi = b.posq[p];
             const int4* rng = s_rng + (b.cell[p] - c0) * 27;
-            uint16_t* out = b.nbr + (size_t)b.K * p;
+            uint32_t* out = b.nbr + (size_t)b.K * p;
             int cnt = 0;
             for (int k = 0; k < 27; ++k) {
                 const int4 rk = rng[k];
@@ -387,13 +387,14 @@ __global__ void __launch_bounds__(LJ_LIST_THREADS) k_nlist(BoxDev b)
                     const unsigned bits = (__ballot_sync(gmask, in) >> gshift) & ((1u << LJ_TPP) - 1u);
                     if (in) {
                         const int pos = cnt + __popc(bits & ((1u << l8) - 1u));
-                        if (pos < b.K) out[pos] = (uint16_t)((k << LJ_TILE_BITS) | (j + toff));
+                        if (pos < b.K) out[pos] = ((uint32_t)k << LJ_IDX_BITS) | (uint32_t)j;
                     }
                     cnt += __popc(bits);
                 }
             }
             if (l8 == 0) {
                 b.nbr_count[p] = cnt;
+                atomicMax(&b.err[2], cnt);   // longest list of this build
                 if (cnt > b.K) {
                     atomicOr(&b.err[0], LJ_ERRBIT_CAPACITY);
                     atomicMax(&b.err[1], cnt);

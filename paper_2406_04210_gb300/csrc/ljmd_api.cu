@@ -99,6 +99,7 @@ struct md_box {
     int64_t chunk_steps = 100;
     // tuning
     int min_capacity = 0;
+    bool autofit = false;      // fit the capacity after the next full build
     int64_t steps = 0;
     int64_t launches = 0;
     bool profiling = false;
@@ -204,6 +205,11 @@ void invalidate_graphs(md_box* b)
 Launch lch(md_box* b) { return Launch{std::max(1, std::min((int)b->d.nchunk, b->nsm * 12)), LJ_CHUNK, b->stream}; }
 Launch lcell(md_box* b) { return Launch{std::max(1, std::min((b->d.ncell + 7) / 8, b->nsm * 8)), 256, b->stream}; }
 Launch lseg(md_box* b) { return Launch{std::max(1, std::min(b->d.nseg, b->nsm * 8)), LJ_SEG_THREADS, b->stream}; }
+Launch lforce(md_box* b)
+{
+    int per_sm = b->prec == 2 ? 12 : 6;
+    return Launch{std::max(1, std::min((int)b->d.nchunk, b->nsm * per_sm)), 0, b->stream};
+}
 Launch llist(md_box* b) { return Launch{std::max(1, std::min(b->d.nseg, b->nsm * 6)), LJ_LIST_THREADS, b->stream}; }
 
 // Fence: internal stream waits for the caller's stream.
@@ -244,14 +250,14 @@ md_status input_ptr(md_box* b, const void* src, size_t bytes, const void** dev, 
 
 md_status read_err(md_box* b, int* err2)
 {
-    CK(b, cudaMemcpyAsync(err2, b->d.err, 2 * sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+    CK(b, cudaMemcpyAsync(err2, b->d.err, 3 * sizeof(int), cudaMemcpyDeviceToHost, b->stream));
     CK(b, cudaStreamSynchronize(b->stream));
     return MD_OK;
 }
 
 md_status clear_err(md_box* b)
 {
-    CK(b, cudaMemsetAsync(b->d.err, 0, 2 * sizeof(int), b->stream));
+    CK(b, cudaMemsetAsync(b->d.err, 0, 3 * sizeof(int), b->stream));
     return MD_OK;
 }
 
@@ -273,7 +279,7 @@ md_status enqueue_rebuild(md_box* b, int from_abs)
 
 md_status enqueue_force(md_box* b, int energy, double* thermo_out_dev)
 {
-    CK(b, launch_force(b->d, energy, lseg(b)));
+    CK(b, launch_force(b->d, energy, lforce(b)));
     b->launches += 1;
     if (energy && thermo_out_dev) {
         Launch lt{std::max(1, std::min(b->nrep, b->nsm * 4)), 512, b->stream};
@@ -298,7 +304,7 @@ md_status alloc_lists(md_box* b, int K)
     if (b->d.nbr) dev_release(b, b->d.nbr);
     b->d.nbr = nullptr;
     b->d.K = K;
-    uint16_t* nb;
+    uint32_t* nb;
     CKS(dev_alloc(b, &nb, (size_t)b->np * (size_t)K + 64, false));
     b->d.nbr = nb;
     invalidate_graphs(b);
@@ -330,9 +336,7 @@ md_status make_segments(md_box* b, bool shrink)
     d.nseg = (int)b->segs.size();
     invalidate_graphs(b);
     dev_release(b, b->d_seg);
-    dev_release(b, d.part_f);
     CKS(dev_alloc(b, &b->d_seg, b->segs.size(), false));
-    CKS(dev_alloc(b, &d.part_f, 2 * b->segs.size()));
     d.seg = b->d_seg;
     CK(b, cudaMemcpyAsync(b->d_seg, b->segs.data(), sizeof(int4) * b->segs.size(),
                           cudaMemcpyHostToDevice, b->stream));
@@ -350,7 +354,7 @@ md_status full_rebuild(md_box* b)
         CKS(clear_err(b));
         CKS(set_all_rebuild(b));
         CKS(enqueue_rebuild(b, b->fresh_abs ? 1 : 0));
-        int e2[2];
+        int e2[3];
         CKS(read_err(b, e2));
         b->binned = true;
         if (e2[0] & LJ_ERRBIT_TIMEOUT) return fail(b, MD_ERR_TIMEOUT, "list build: device wait timed out");
@@ -366,6 +370,16 @@ md_status full_rebuild(md_box* b)
             continue;
         }
         b->fresh_abs = true;
+        // automatic capacity: fit it to the longest list (+10 % and 8) so
+        // the padded rows the force kernel streams stay short
+        if (b->min_capacity == 0 && b->autofit) {
+            int Kfit = round_up((int64_t)(e2[2] * 1.1) + 8, 8);
+            b->autofit = false;
+            if (Kfit + 8 < b->d.K) {
+                CKS(alloc_lists(b, Kfit));
+                continue;
+            }
+        }
         CKS(enqueue_force(b, 0, nullptr));
         return MD_OK;
     }
@@ -439,7 +453,7 @@ md_status enqueue_steps(md_box* b, int64_t n, double dt, int energy, double* rin
         CKS(enqueue_rebuild(b, 0));
         CK(b, mark(s, 1, 1));
         CK(b, mark(s, 2, 0));
-        CK(b, launch_force(b->d, energy, lseg(b)));
+        CK(b, launch_force(b->d, energy, lforce(b)));
         CK(b, mark(s, 2, 1));
         b->launches += 1;
     }
@@ -616,8 +630,9 @@ md_status md_batch_create(md_box** out, int32_t nrep, const int64_t* n, const do
         CKS(dev_alloc(b, &d.rebuild_req, nrep));
         CKS(dev_alloc(b, &d.any_req, 1));
         CKS(dev_alloc(b, &d.nbuild, nrep));
-        CKS(dev_alloc(b, &d.err, 2));
+        CKS(dev_alloc(b, &d.err, 4));
         CKS(dev_alloc(b, &d.part_k, std::max<size_t>(1, b->chunks.size())));
+        CKS(dev_alloc(b, &d.part_f, 2 * std::max<size_t>(1, b->chunks.size())));
         CKS(dev_alloc(b, &b->d_type_user, std::max<int64_t>(1, ntot)));
         CK(b, cudaMemcpyAsync(b->d_rep, b->reps.data(), sizeof(RepDev) * b->reps.size(),
                               cudaMemcpyHostToDevice, b->stream));
@@ -799,6 +814,7 @@ md_status md_set_lj(md_box* b, int32_t ntypes, const double* eps, const double* 
         int K = round_up((int64_t)(1.3 * expect) + 16, 8);
         if (b->min_capacity > 0) K = round_up(b->min_capacity, 8);
         CKS(alloc_lists(b, K));
+        b->autofit = true;
     }
     b->lj_set = true;
     CKS(full_rebuild(b));
@@ -846,7 +862,7 @@ md_status md_force(md_box* b, double* force_out, double* epot, double* virial)
     std::vector<double> th(4 * (size_t)b->nrep);
     CK(b, cudaMemcpyAsync(th.data(), b->d_thermo, sizeof(double) * th.size(), cudaMemcpyDeviceToHost,
                           b->stream));
-    int e2[2];
+    int e2[3];
     CKS(read_err(b, e2));
     CKS(leave(b));
     for (int r = 0; r < b->nrep; ++r) {
@@ -879,7 +895,7 @@ md_status md_integrate(md_box* b, double dt, int64_t nsteps, int32_t ckpt_every,
         cudaGraphExec_t g;
         CKS(get_graph(b, n, dt, energy, &g));
         CK(b, cudaGraphLaunch(g, b->stream));
-        int e2[2];
+        int e2[3];
         CKS(read_err(b, e2));
         for (auto& ge : b->graphs)
             if (ge.exec == g) {
@@ -995,7 +1011,7 @@ md_status md_get_nlist(md_box* b, int32_t* count, int64_t* nbr, int64_t cap, dou
     long long* tn = nbr ? reinterpret_cast<long long*>(st + ((cb + 255) & ~(size_t)255)) : nullptr;
     double* tp = pos ? reinterpret_cast<double*>(st + ((cb + 255) & ~(size_t)255) + ((nb + 255) & ~(size_t)255))
                      : nullptr;
-    CK(b, launch_get_nlist(b->d, tc, tn, (long long)cap, tp, lseg(b)));
+    CK(b, launch_get_nlist(b->d, tc, tn, (long long)cap, tp, lch(b)));
     std::vector<int> hc(b->ntot);
     CK(b, cudaMemcpyAsync(hc.data(), tc, cb, cudaMemcpyDeviceToHost, b->stream));
     if (nbr) CK(b, cudaMemcpyAsync(nbr, tn, nb, is_device_ptr(nbr) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, b->stream));

@@ -15,12 +15,15 @@
 //     contiguous slot range, and the 27-cell neighbourhood of all its cells
 //     is the "tile": 9 rows x (S + 2) cells, i.e. at most 18 contiguous slot
 //     ranges ("pieces"), staged in shared memory.
-//   * Verlet lists (Sec. 3) are 16-bit entries (stencil code << 11 | tile
-//     index), so a tile holds at most 2048 particles.  The stencil code
-//     k = 9(dz+1) + 3(dy+1) + (dx+1) names the image shift of j's cell
-//     relative to i's cell, so d_ij = (o_i - o_j) - shift(k).  Entry s of
-//     particle p is nbr[p K + s] (K a multiple of 8): each thread streams its
-//     own list in 16-byte groups of 8 entries, several groups in flight.
+//   * Verlet lists (Sec. 3) are 32-bit entries (stencil code << 27 | slot j).
+//     The stencil code k = 9(dz+1) + 3(dy+1) + (dx+1) names the image shift
+//     of j's cell relative to i's cell, so d_ij = (o_i - o_j) - shift(k).
+//     Entry s of particle p is nbr[p K + s] (K a multiple of 8): the 8 threads
+//     of a particle read 8 consecutive entries (one 32-byte sector) at a time.
+//   * the list build works per segment with the tile staged in shared memory;
+//     the pair-force kernels work per 128-particle chunk, 8 threads per
+//     particle, and gather neighbour offsets through L1 (the 32 particles of a
+//     block pass are consecutive, so they share one 27-cell neighbourhood).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -28,18 +31,21 @@
 
 #define LJ_MAXT 8
 #define LJ_IDX_BITS 27         // slot indices must stay below 2^27
+#define LJ_IDX_MASK ((1u << LJ_IDX_BITS) - 1u)
 #define LJ_TILE_BITS 11
 #define LJ_TILE_MAX (1 << LJ_TILE_BITS)
 #define LJ_TILE_MASK (LJ_TILE_MAX - 1)
 #define LJ_CHUNK 128           // particles per work item (one CTA pass)
-#define LJ_SEG_THREADS 256     // threads of the segment pair kernels
+#define LJ_SEG_THREADS 256     // threads of the segment kernels
+#define LJ_FORCE_THREADS 256   // threads of the FP32 pair-force kernel
 #define LJ_LIST_THREADS 256    // threads of the list-build kernel
 #define LJ_F64_THREADS 128     // threads of the FP64 pair kernel (one per particle)
 #define LJ_TPP 8               // threads per particle in the pair kernels
 #define LJ_SEG_MAX_CELLS 16    // most cells in one segment
 #define LJ_LIST_SMEM (32 * 1024)   // bytes of a segment's list staged in smem
 
-// error word bits (err[0]); err[1] = largest list length seen
+// error word bits (err[0]); err[1] = largest list length beyond capacity;
+// err[2] = longest list of the last builds
 #define LJ_ERRBIT_CAPACITY 1
 #define LJ_ERRBIT_NONFINITE 2
 #define LJ_ERRBIT_TIMEOUT 4
@@ -128,7 +134,7 @@ struct BoxDev {
     int* cell_end;
     const int* cell_rep;
     // lists
-    uint16_t* nbr;
+    uint32_t* nbr;
     int* nbr_count;
     // per-replica control
     unsigned* disp_max;        // FP32 bits of the largest |displacement|^2
@@ -137,7 +143,7 @@ struct BoxDev {
     unsigned long long* nbuild;
     int* err;
     // per-chunk FP64 partial sums
-    double* part_f;            // [seg*2 + 0] = E_pot share, [+1] = W share
+    double* part_f;            // [chunk*2 + 0] = E_pot share, [+1] = W share
     double* part_k;            // [chunk] = E_kin share
 };
 
