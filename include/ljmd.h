@@ -149,12 +149,29 @@ md_status md_integrate(md_box* b, double dt, int64_t nsteps, int32_t ckpt_every,
  *                     symmetric parameter eps_ab (sigma_ab), rcut held fixed.
  * The paper has no adjoint; this follows from differentiating the steps
  * above (velocity-Verlet is differentiated exactly, one Hessian-vector
- * product of U per step).  Returns MD_ERR_STATE if no recorded run exists.
- * Only MD_PREC_MIXED_DS / MD_PREC_MIXED_FP64 / MD_PREC_FP64 single-replica
- * and batched boxes are supported alike. */
+ * product of U per step, evaluated in FP32 with the recorded lists; the
+ * adjoint state is FP64).  Each segment of ckpt_every steps is replayed from
+ * its checkpoint bit for bit (a recorded run rebuilds the lists at every
+ * checkpoint).  Returns MD_ERR_STATE if no recorded run exists (recording is
+ * dropped by md_set_lj and md_set_state).  The box's state after the call is
+ * the end-of-run state.  Batched boxes return parameter gradients summed
+ * over replicas (the parameters are shared). */
 md_status md_adjoint(md_box* b, const double* lam_x_T, const double* lam_v_T,
                      double* lam_x_0, double* lam_v_0, double* dL_deps,
                      double* dL_dsigma);
+
+/* Smoothed pair-distance histogram of the current positions and its
+ * gradient, a trajectory loss for md_adjoint (no counterpart in the paper):
+ *   h[r, k] = (1/n_r) sum_{i<j in replica r, r_ij < rmax} exp(-(r_ij - c_k)^2 / (2 width^2)),
+ *   c_k = (k + 1/2) rhist / nbins,  k = 0 .. nbins-1  (1 <= nbins <= 256)
+ *   hist  nullable, nrep x nbins FP64 out
+ *   coef  nullable, nrep x nbins FP64: with grad, grad receives
+ *         d/dx sum_{r,k} coef[r,k] h[r,k], (sum n) x 3 FP64, user order
+ * rmax must not exceed the list radius (rcut + skin); the lists are rebuilt
+ * first if the particles moved since the last build.  Distances are FP32. */
+md_status md_pair_hist(md_box* b, int32_t nbins, double rhist, double width,
+                       double rmax, const double* coef, double* hist,
+                       double* grad);
 
 /* Current state in user order: pos in [0, L) FP64, vel FP64, image counts
  * (number of box lengths crossed), each nullable. */

@@ -105,6 +105,30 @@ struct md_box {
     bool profiling = false;
     double prof_ms[4] = {0, 0, 0, 0};
     int64_t prof_n[4] = {0, 0, 0, 0};
+    // recorded forward run (md_integrate with ckpt_every > 0)
+    bool rec_valid = false;
+    int64_t rec_nsteps = 0;
+    int rec_k = 0, rec_C = 0;
+    double rec_dt = 0.0;
+    std::vector<std::pair<void*, size_t>> ck_src;   // arrays saved per checkpoint
+    char* d_ckpt = nullptr;
+    size_t ckpt_bytes = 0;
+    int ckpt_cap = 0;
+    // adjoint work arrays
+    double* d_lx = nullptr;
+    double* d_lv = nullptr;
+    double* d_g = nullptr;
+    double* d_theta = nullptr;
+    double* d_wts = nullptr;
+    double* d_partg = nullptr;
+    float4* d_u = nullptr;
+    float4* d_hu = nullptr;
+    char* d_tape = nullptr;
+    size_t tape_step_bytes = 0;
+    int tape_cap = 0;
+    double* d_parth = nullptr;
+    double* d_hist = nullptr;
+    int hist_cap = 0;
     std::string err;
 };
 
@@ -424,7 +448,41 @@ md_status snapshot(md_box* b, bool restore)
 // The velocity-Verlet loop for `n` steps (Sec. 3, Fig. 1): integrate,
 // conditional list update, force, finalize (fused with the next integrate).
 // With `ge` set, events bracket every phase of every step (profiling).
-md_status enqueue_steps(md_box* b, int64_t n, double dt, int energy, double* ring, GraphEnt* ge)
+size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Copy the state a Hessian-vector product needs (FP32 offsets, slot -> user
+// map, lists) into tape slot m.
+md_status tape_save(md_box* b, int m)
+{
+    const size_t np = (size_t)b->np;
+    char* t = b->d_tape + (size_t)m * b->tape_step_bytes;
+    CK(b, cudaMemcpyAsync(t, b->d.posq, np * 16, cudaMemcpyDeviceToDevice, b->stream));
+    t += al256(np * 16);
+    CK(b, cudaMemcpyAsync(t, b->d.uid, np * 4, cudaMemcpyDeviceToDevice, b->stream));
+    t += al256(np * 4);
+    CK(b, cudaMemcpyAsync(t, b->d.nbr_count, np * 4, cudaMemcpyDeviceToDevice, b->stream));
+    t += al256(np * 4);
+    CK(b, cudaMemcpyAsync(t, b->d.nbr, np * (size_t)b->d.K * 4, cudaMemcpyDeviceToDevice, b->stream));
+    return MD_OK;
+}
+
+BoxDev tape_view(md_box* b, int m)
+{
+    const size_t np = (size_t)b->np;
+    BoxDev v = b->d;
+    char* t = b->d_tape + (size_t)m * b->tape_step_bytes;
+    v.posq = reinterpret_cast<float4*>(t);
+    t += al256(np * 16);
+    v.uid = reinterpret_cast<int*>(t);
+    t += al256(np * 4);
+    v.nbr_count = reinterpret_cast<int*>(t);
+    t += al256(np * 4);
+    v.nbr = reinterpret_cast<uint32_t*>(t);
+    return v;
+}
+
+md_status enqueue_steps(md_box* b, int64_t n, double dt, int energy, double* ring, GraphEnt* ge,
+                        bool tape = false)
 {
     Launch l = lch(b);
     Launch lt{std::max(1, std::min(b->nrep, b->nsm * 4)), 512, b->stream};
@@ -456,7 +514,62 @@ md_status enqueue_steps(md_box* b, int64_t n, double dt, int energy, double* rin
         CK(b, launch_force(b->d, energy, lforce(b)));
         CK(b, mark(s, 2, 1));
         b->launches += 1;
+        if (tape) CKS(tape_save(b, (int)s + 1));
     }
+    return MD_OK;
+}
+
+// ------------------------------------------------------------------------
+// Checkpoints of a recorded run.  A checkpoint is taken right after a forced
+// list build, so restoring it and rebuilding only the lists (k_nlist from the
+// saved offsets, cell ranges and build positions) reproduces the recorded
+// state bit for bit.
+// ------------------------------------------------------------------------
+md_status ckpt_setup(md_box* b, int C)
+{
+    const size_t np = (size_t)b->np, nc = (size_t)b->d.ncell;
+    b->ck_src.clear();
+    b->ck_src.push_back({b->d.off, 24 * np});
+    b->ck_src.push_back({b->d.vel, 24 * np});
+    b->ck_src.push_back({b->d.img, 12 * np});
+    b->ck_src.push_back({b->d.uid, 4 * np});
+    b->ck_src.push_back({b->d.type, 4 * np});
+    b->ck_src.push_back({b->d.cell, 4 * np});
+    b->ck_src.push_back({b->d.posq, 16 * np});
+    b->ck_src.push_back({b->d.ref, 16 * np});
+    b->ck_src.push_back({b->d.xabs, 24 * np});
+    b->ck_src.push_back({b->d.cell_start, 4 * nc});
+    b->ck_src.push_back({b->d.cell_end, 4 * nc});
+    size_t per = 0;
+    for (auto& a : b->ck_src) per += al256(a.second);
+    if (b->ckpt_bytes != per || b->ckpt_cap < C) {
+        dev_release(b, b->d_ckpt);
+        b->d_ckpt = nullptr;
+        CKS(dev_alloc(b, &b->d_ckpt, per * (size_t)C, false));
+        b->ckpt_bytes = per;
+        b->ckpt_cap = C;
+    }
+    return MD_OK;
+}
+
+md_status ckpt_copy(md_box* b, int c, bool restore)
+{
+    char* base = b->d_ckpt + (size_t)c * b->ckpt_bytes;
+    for (auto& a : b->ck_src) {
+        if (restore) CK(b, cudaMemcpyAsync(a.first, base, a.second, cudaMemcpyDeviceToDevice, b->stream));
+        else CK(b, cudaMemcpyAsync(base, a.first, a.second, cudaMemcpyDeviceToDevice, b->stream));
+        base += al256(a.second);
+    }
+    return MD_OK;
+}
+
+// Lists from the restored build state, then the forces (no re-binning).
+md_status replay_lists(md_box* b)
+{
+    CKS(set_all_rebuild(b));
+    CK(b, launch_nlist(b->d, llist(b)));
+    CK(b, launch_force(b->d, 0, lforce(b)));
+    b->launches += 2;
     return MD_OK;
 }
 
@@ -729,6 +842,12 @@ md_status md_set_lj(md_box* b, int32_t ntypes, const double* eps, const double* 
         double c6 = (s2 / rc2) * (s2 / rc2) * (s2 / rc2);
         double sh = energy_shift ? 4.0 * eps[k] * (c6 * c6 - c6) : 0.0;
         double s6 = s2 * s2 * s2;
+        double sg = sigma[k];
+        h.a12[k] = (float)(672.0 * eps[k] * s6 * s6);
+        h.a6[k] = (float)(192.0 * eps[k] * s6);
+        h.g12[k] = (float)(576.0 * eps[k] * s6 * s6 / sg);
+        h.g6[k] = (float)(144.0 * eps[k] * s6 / sg);
+        h.inv_eps[k] = (float)(1.0 / eps[k]);
         h.c12[k] = (float)(48.0 * eps[k] * s6 * s6);
         h.c6[k] = (float)(24.0 * eps[k] * s6);
         h.e12[k] = (float)(4.0 * eps[k] * s6 * s6);
@@ -817,6 +936,7 @@ md_status md_set_lj(md_box* b, int32_t ntypes, const double* eps, const double* 
         b->autofit = true;
     }
     b->lj_set = true;
+    b->rec_valid = false;
     CKS(full_rebuild(b));
     CKS(leave(b));
     return MD_OK;
@@ -878,18 +998,27 @@ md_status md_integrate(md_box* b, double dt, int64_t nsteps, int32_t ckpt_every,
 {
     if (!b || !b->lj_set) return fail(b, MD_ERR_ARG, "md_integrate: md_set_lj not called");
     if (!(dt > 0.0) || nsteps < 0 || ckpt_every < 0) return fail(b, MD_ERR_ARG, "md_integrate: bad arguments");
-    if (ckpt_every > 0) return fail(b, MD_ERR_ARG, "md_integrate: recording not available");
+    if (ckpt_every > 0 && nsteps % ckpt_every != 0)
+        return fail(b, MD_ERR_ARG, "md_integrate: nsteps must be a multiple of ckpt_every");
     if (nsteps == 0) return MD_OK;
     CKS(enter(b));
-    b->fresh_abs = false;   // offsets advance; xabs keeps the last build
+    const bool record = ckpt_every > 0;
+    b->rec_valid = false;
+    if (record) CKS(ckpt_setup(b, (int)(nsteps / ckpt_every)));
     const int energy = thermo_out ? 1 : 0;
-    const int64_t chunk = b->chunk_steps;
+    const int64_t chunk = record ? ckpt_every : b->chunk_steps;
     if (energy) CKS(ensure_thermo(b, std::min(nsteps, chunk)));
     bool out_dev = energy && is_device_ptr(thermo_out);
     int64_t done = 0;
     int retries = 0;
     while (done < nsteps) {
         int64_t n = std::min(chunk, nsteps - done);
+        if (record) {
+            // checkpoint boundary: fresh lists, then save the build state
+            CKS(full_rebuild(b));
+            CKS(ckpt_copy(b, (int)(done / ckpt_every), false));
+        }
+        b->fresh_abs = false;   // offsets advance; xabs keeps the last build
         CKS(clear_err(b));
         CKS(snapshot(b, false));
         cudaGraphExec_t g;
@@ -936,13 +1065,158 @@ md_status md_integrate(md_box* b, double dt, int64_t nsteps, int32_t ckpt_every,
         done += n;
         b->steps += n;
     }
+    if (record) {
+        b->rec_valid = true;
+        b->rec_nsteps = nsteps;
+        b->rec_k = ckpt_every;
+        b->rec_C = (int)(nsteps / ckpt_every);
+        b->rec_dt = dt;
+    }
     CKS(leave(b));
     return MD_OK;
 }
 
-md_status md_adjoint(md_box* b, const double*, const double*, double*, double*, double*, double*)
+md_status md_adjoint(md_box* b, const double* lam_x_T, const double* lam_v_T, double* lam_x_0,
+                     double* lam_v_0, double* dL_deps, double* dL_dsigma)
 {
-    return fail(b, MD_ERR_STATE, "md_adjoint: no recorded forward run");
+    if (!b) return MD_ERR_ARG;
+    if (!b->rec_valid || !b->lj_set) return fail(b, MD_ERR_STATE, "md_adjoint: no recorded forward run");
+    if (!lam_x_T || !lam_v_T || !lam_x_0 || !lam_v_0) return fail(b, MD_ERR_ARG, "md_adjoint: null array");
+    CKS(enter(b));
+    const size_t n3 = 3 * (size_t)b->ntot, np = (size_t)b->np;
+    const int k = b->rec_k, C = b->rec_C;
+    const double h = b->rec_dt;
+    const int P = b->nt * b->nt;
+    if (!b->d_lx) {
+        CKS(dev_alloc(b, &b->d_lx, n3));
+        CKS(dev_alloc(b, &b->d_lv, n3));
+        CKS(dev_alloc(b, &b->d_g, n3));
+        CKS(dev_alloc(b, &b->d_u, np));
+        CKS(dev_alloc(b, &b->d_hu, np));
+        CKS(dev_alloc(b, &b->d_theta, 2 * LJ_MAXT * LJ_MAXT));
+        CKS(dev_alloc(b, &b->d_wts, 2));
+        CKS(dev_alloc(b, &b->d_partg, 2 * (size_t)LJ_MAXT * LJ_MAXT * std::max<size_t>(1, b->chunks.size())));
+    }
+    size_t step_bytes = al256(np * 16) + 2 * al256(np * 4) + al256(np * (size_t)b->d.K * 4);
+    if (b->tape_step_bytes != step_bytes || b->tape_cap < k + 1) {
+        dev_release(b, b->d_tape);
+        b->d_tape = nullptr;
+        CKS(dev_alloc(b, &b->d_tape, step_bytes * (size_t)(k + 1), false));
+        b->tape_step_bytes = step_bytes;
+        b->tape_cap = k + 1;
+    }
+    const double wts[2] = {0.5 * h, h};
+    CK(b, cudaMemcpyAsync(b->d_wts, wts, sizeof wts, cudaMemcpyHostToDevice, b->stream));
+    CK(b, cudaMemsetAsync(b->d_theta, 0, sizeof(double) * 2 * LJ_MAXT * LJ_MAXT, b->stream));
+    const void *ix, *iv;
+    CKS(ensure_stage(b, 2 * n3 * sizeof(double)));
+    CKS(input_ptr(b, lam_x_T, n3 * sizeof(double), &ix, 0));
+    CKS(input_ptr(b, lam_v_T, n3 * sizeof(double), &iv, n3 * sizeof(double)));
+    CK(b, cudaMemcpyAsync(b->d_lx, ix, n3 * sizeof(double), cudaMemcpyDeviceToDevice, b->stream));
+    CK(b, cudaMemcpyAsync(b->d_lv, iv, n3 * sizeof(double), cudaMemcpyDeviceToDevice, b->stream));
+    CK(b, cudaStreamSynchronize(b->stream));   // host inputs staged before reuse
+    // keep the current (end of run) state; restored at the end
+    CKS(snapshot(b, false));
+    Launch l = lch(b);
+    Launch lf = lforce(b);
+    const int nchunk = (int)b->chunks.size();
+    const int twoP = 2 * P;
+    for (int c = C - 1; c >= 0; --c) {
+        // replay segment c, keeping every state's HVP inputs on the tape
+        CKS(ckpt_copy(b, c, true));
+        CKS(clear_err(b));
+        CKS(replay_lists(b));
+        CKS(tape_save(b, 0));
+        CKS(enqueue_steps(b, k, h, 0, nullptr, nullptr, true));
+        int e2[3];
+        CKS(read_err(b, e2));
+        if (e2[0]) return fail(b, MD_ERR_CAPACITY, "md_adjoint: replay of a segment failed");
+        for (int m = k; m >= 0; --m) {
+            BoxDev v = tape_view(b, m);
+            if (m == k) {
+                if (c != C - 1) continue;   // this state's HVP was done at m = 0 of segment c + 1
+                CK(b, launch_adj_pre(v, b->d_lx, b->d_lv, b->d_g, b->d_u, h, 0, l));
+                CK(b, launch_hvp(v, b->d_u, b->d_hu, b->d_partg, lf));
+                CK(b, launch_adj_post(v, b->d_lx, b->d_g, b->d_hu, h, 0, l));
+                CK(b, launch_param_reduce(b->d_partg, nchunk, twoP, b->d_wts, b->d_theta, b->stream));
+            } else {
+                const bool first = (c == 0 && m == 0);
+                CK(b, launch_adj_pre(v, b->d_lx, b->d_lv, b->d_g, b->d_u, h, 1, l));
+                CK(b, launch_hvp(v, b->d_u, b->d_hu, b->d_partg, lf));
+                CK(b, launch_adj_post(v, b->d_lx, b->d_g, b->d_hu, h, 1, l));
+                CK(b, launch_param_reduce(b->d_partg, nchunk, twoP, b->d_wts + (first ? 0 : 1), b->d_theta,
+                                          b->stream));
+            }
+            b->launches += 4;
+        }
+    }
+    // outputs
+    bool dx = is_device_ptr(lam_x_0), dv = is_device_ptr(lam_v_0);
+    CK(b, cudaMemcpyAsync(lam_x_0, b->d_lx, n3 * sizeof(double), dx ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                          b->stream));
+    CK(b, cudaMemcpyAsync(lam_v_0, b->d_lv, n3 * sizeof(double), dv ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                          b->stream));
+    std::vector<double> th(2 * (size_t)P);
+    CK(b, cudaMemcpyAsync(th.data(), b->d_theta, sizeof(double) * 2 * P, cudaMemcpyDeviceToHost, b->stream));
+    // back to the end-of-run state
+    CKS(snapshot(b, true));
+    CKS(full_rebuild(b));
+    b->fresh_abs = false;
+    CKS(leave(b));
+    const int nt = b->nt;
+    std::vector<double> ge(P), gs(P);
+    for (int a = 0; a < nt; ++a)
+        for (int q = 0; q < nt; ++q) {
+            int lo = std::min(a, q), hi = std::max(a, q);
+            ge[a * nt + q] = th[lo * nt + hi];
+            gs[a * nt + q] = th[P + lo * nt + hi];
+        }
+    if (dL_deps) {
+        if (is_device_ptr(dL_deps)) CK(b, cudaMemcpy(dL_deps, ge.data(), sizeof(double) * P, cudaMemcpyHostToDevice));
+        else std::memcpy(dL_deps, ge.data(), sizeof(double) * P);
+    }
+    if (dL_dsigma) {
+        if (is_device_ptr(dL_dsigma)) CK(b, cudaMemcpy(dL_dsigma, gs.data(), sizeof(double) * P, cudaMemcpyHostToDevice));
+        else std::memcpy(dL_dsigma, gs.data(), sizeof(double) * P);
+    }
+    return MD_OK;
+}
+
+md_status md_pair_hist(md_box* b, int32_t nbins, double rhist, double width, double rmax, const double* coef,
+                       double* hist, double* grad)
+{
+    if (!b || !b->lj_set || nbins < 1 || nbins > 256 || !(rhist > 0) || !(width > 0) || !(rmax > 0))
+        return fail(b, MD_ERR_ARG, "md_pair_hist: bad arguments");
+    if (rmax > b->rl) return fail(b, MD_ERR_ARG, "md_pair_hist: rmax beyond the list radius");
+    CKS(enter(b));
+    // the lists must hold every pair below rmax at the current positions
+    if (!b->fresh_abs) CKS(full_rebuild(b));
+    const size_t nh = (size_t)b->nrep * nbins;
+    if (b->hist_cap < nbins) {
+        dev_release(b, b->d_parth);
+        dev_release(b, b->d_hist);
+        CKS(dev_alloc(b, &b->d_parth, (size_t)nbins * std::max<size_t>(1, b->chunks.size())));
+        CKS(dev_alloc(b, &b->d_hist, (size_t)b->nrep * nbins));
+        b->hist_cap = nbins;
+    }
+    if (hist) {
+        CK(b, launch_pair_hist(b->d, nbins, rhist, width, rmax, b->d_parth, b->d_hist, lch(b)));
+        CK(b, cudaMemcpyAsync(hist, b->d_hist, sizeof(double) * nh,
+                              is_device_ptr(hist) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, b->stream));
+        b->launches += 2;
+    }
+    if (grad && coef && b->ntot > 0) {
+        const size_t gb = sizeof(double) * 3 * (size_t)b->ntot;
+        CKS(ensure_stage(b, gb + sizeof(double) * nh + 256));
+        const void* dc;
+        CKS(input_ptr(b, coef, sizeof(double) * nh, &dc, al256(gb)));
+        double* dg = is_device_ptr(grad) ? grad : reinterpret_cast<double*>(b->d_stage);
+        CK(b, launch_pair_hist_grad(b->d, nbins, rhist, width, rmax, static_cast<const double*>(dc), dg, lch(b)));
+        b->launches += 1;
+        if (dg != grad) CK(b, cudaMemcpyAsync(grad, dg, gb, cudaMemcpyDeviceToHost, b->stream));
+    }
+    CKS(leave(b));
+    return MD_OK;
 }
 
 md_status md_get_state(md_box* b, double* pos, double* vel, int32_t* image)
@@ -991,6 +1265,7 @@ md_status md_set_state(md_box* b, const double* pos, const double* vel)
     CK(b, launch_upload(b->d, static_cast<const double*>(dpos), dvel, b->d_type_user,
                         (vel || b->binned) ? 1 : 0, lch(b)));
     b->fresh_abs = true;
+    b->rec_valid = false;
     if (b->lj_set) CKS(full_rebuild(b));
     CKS(leave(b));
     return MD_OK;

@@ -86,6 +86,10 @@ struct LJDev {
     int shift_on;
     // FP32 lj1/lj2 form: f = r2i r6i (c12 r6i - c6), u = r6i (e12 r6i - e6) - shift
     float c12[LJ_MAXT * LJ_MAXT], c6[LJ_MAXT * LJ_MAXT], e12[LJ_MAXT * LJ_MAXT], e6[LJ_MAXT * LJ_MAXT];
+    // Hessian and parameter-derivative coefficients (adjoint):
+    // A = r2i^2 r6i (a12 r6i - a6); dF/dsigma coefficient r2i r6i (g12 r6i - g6)
+    float a12[LJ_MAXT * LJ_MAXT], a6[LJ_MAXT * LJ_MAXT], g12[LJ_MAXT * LJ_MAXT], g6[LJ_MAXT * LJ_MAXT];
+    float inv_eps[LJ_MAXT * LJ_MAXT];
     float sig2[LJ_MAXT * LJ_MAXT], eps48[LJ_MAXT * LJ_MAXT], eps4[LJ_MAXT * LJ_MAXT];
     float rc2[LJ_MAXT * LJ_MAXT], shift[LJ_MAXT * LJ_MAXT];
     double dsig2[LJ_MAXT * LJ_MAXT], deps48[LJ_MAXT * LJ_MAXT], deps4[LJ_MAXT * LJ_MAXT];
@@ -339,7 +343,19 @@ cudaError_t launch_nlist(const BoxDev& b, Launch l);
 // k_force.cu
 cudaError_t launch_force(const BoxDev& b, int energy, Launch l);
 cudaError_t launch_thermo(const BoxDev& b, double* out, int with_kin, Launch l);
-cudaError_t launch_hvp(const BoxDev& b, const double* u, double* hu, double* part_g, Launch l);
+
+// k_adjoint.cu
+cudaError_t launch_adj_pre(const BoxDev& b, double* lx, double* lv, const double* g, float4* u_slot, double h,
+                           int pre, Launch l);
+cudaError_t launch_adj_post(const BoxDev& b, double* lx, double* g, const float4* hu_slot, double h, int upd,
+                            Launch l);
+cudaError_t launch_hvp(const BoxDev& b, const float4* u_slot, float4* hu_slot, double* part_g, Launch l);
+cudaError_t launch_param_reduce(const double* part_g, int nchunk, int twoP, const double* weight,
+                                double* theta_grad, cudaStream_t s);
+cudaError_t launch_pair_hist(const BoxDev& b, int nbins, double rhist, double width, double rmax, double* part_h,
+                             double* h, Launch l);
+cudaError_t launch_pair_hist_grad(const BoxDev& b, int nbins, double rhist, double width, double rmax,
+                                  const double* coef, double* grad, Launch l);
 
 // k_integrate.cu
 cudaError_t launch_integrate(const BoxDev& b, int mode, int energy, double dt, Launch l);

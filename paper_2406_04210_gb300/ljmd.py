@@ -29,7 +29,8 @@ STATUS = {0: "MD_OK", 1: "MD_ERR_ARG", 2: "MD_ERR_CUDA", 3: "MD_ERR_OOM", 4: "MD
 EXPORTS = ["md_set_allocator", "md_batch_create", "md_box_create", "md_box_destroy",
            "md_set_lj", "md_neighbour_update", "md_force", "md_integrate", "md_adjoint",
            "md_get_state", "md_set_state", "md_get_nlist", "md_get_info", "md_set_tuning",
-           "md_set_profiling", "md_get_profile", "md_last_error", "md_status_string"]
+           "md_set_profiling", "md_get_profile", "md_pair_hist", "md_last_error",
+           "md_status_string"]
 
 
 class LibraryMissing(RuntimeError):
@@ -89,6 +90,7 @@ def load(path: str | None = None):
         L.md_get_info.argtypes = [vp, ctypes.POINTER(Info)]
         L.md_set_tuning.argtypes = [vp, i32, i32, i32]
         L.md_set_profiling.argtypes = [vp, i32]
+        L.md_pair_hist.argtypes = [vp, i32, d, d, d, vp, vp, vp]
         L.md_get_profile.argtypes = [vp, vp, vp]
         L.md_last_error.argtypes = [vp]
         L.md_last_error.restype = ctypes.c_char_p
@@ -203,6 +205,7 @@ class Box:
 
     # -- ABI wrappers --
     def set_lj(self, eps=1.0, sigma=1.0, rcut=2.5, skin=0.3, shift=True):
+        self._rcut, self._skin = rcut, skin
         eps = np.ascontiguousarray(np.atleast_2d(eps), dtype=np.float64)
         sigma = np.ascontiguousarray(np.atleast_2d(sigma), dtype=np.float64)
         rcut = np.ascontiguousarray(np.atleast_2d(rcut), dtype=np.float64)
@@ -246,6 +249,20 @@ class Box:
         self._check(self._lib.md_adjoint(self._h, a, b, lx0.ctypes.data, lv0.ctypes.data,
                                          ge.ctypes.data, gs.ctypes.data), "md_adjoint")
         return lx0, lv0, ge, gs
+
+    def pair_hist(self, nbins=64, rhist=2.5, width=None, rmax=2.8, coef=None):
+        """Smoothed pair-distance histogram (nrep x nbins) and, with coef, the
+        gradient of sum(coef * h) with respect to the positions."""
+        width = rhist / nbins if width is None else width
+        h = np.zeros((self.nrep, nbins))
+        g = np.zeros((self.n_total, 3)) if coef is not None else None
+        c = np.ascontiguousarray(np.broadcast_to(np.asarray(coef, dtype=np.float64),
+                                                 (self.nrep, nbins))) if coef is not None else None
+        pc, kc = _ptr(c)
+        pg, kg = _ptr(g)
+        self._check(self._lib.md_pair_hist(self._h, int(nbins), float(rhist), float(width),
+                                           float(rmax), pc, h.ctypes.data, pg), "md_pair_hist")
+        return h, g
 
     def get_state(self):
         pos = np.zeros((self.n_total, 3))
@@ -309,3 +326,87 @@ def from_system(s, precision="mixed_ds"):
     b = Box(s.pos, s.box, s.vel, s.type, precision=precision)
     b.set_lj(s.eps, s.sigma, s.rcut, s.skin, True)
     return b
+
+
+# ---------------------------------------------------------------------------
+# torch.autograd bridge: trajectories and the pair-histogram loss
+# ---------------------------------------------------------------------------
+def _torch():
+    import torch
+    return torch
+
+
+class TrajectoryFn:
+    """x_T, v_T = TrajectoryFn.apply(x0, v0, eps, sigma, box, dt, nsteps, ckpt_every)
+
+    Forward: md_set_state(x0, v0), md_set_lj(eps, sigma) (monatomic: scalar
+    tensors; the box's cutoff and skin are kept), then a recorded
+    md_integrate.  Backward: md_adjoint.  x0, v0 are (n, 3) float64 CUDA
+    tensors; eps, sigma are 0-d float64 tensors."""
+
+    _fn = None
+
+    @classmethod
+    def apply(cls, *args):
+        if cls._fn is None:
+            torch = _torch()
+
+            class _F(torch.autograd.Function):
+                @staticmethod
+                def forward(ctx, x0, v0, eps, sigma, box, dt, nsteps, ckpt_every):
+                    box.set_lj(float(eps), float(sigma), box._rcut, box._skin, True)
+                    box.set_state(x0.detach().contiguous(), v0.detach().contiguous())
+                    box.integrate(dt, nsteps, thermo=False, ckpt_every=ckpt_every)
+                    xT = torch.empty_like(x0)
+                    vT = torch.empty_like(v0)
+                    box._check(box._lib.md_get_state(box._h, xT.data_ptr(), vT.data_ptr(), None),
+                               "md_get_state")
+                    ctx.box = box
+                    return xT, vT
+
+                @staticmethod
+                def backward(ctx, gx, gv):
+                    box = ctx.box
+                    gx = torch.zeros_like(gv) if gx is None else gx.contiguous()
+                    gv = torch.zeros_like(gx) if gv is None else gv.contiguous()
+                    lx0, lv0, ge, gs = box.adjoint(gx, gv)
+                    dev = gx.device
+                    return (torch.from_numpy(lx0).to(dev), torch.from_numpy(lv0).to(dev),
+                            torch.tensor(ge[0, 0], dtype=torch.float64, device=dev),
+                            torch.tensor(gs[0, 0], dtype=torch.float64, device=dev),
+                            None, None, None, None)
+
+            cls._fn = _F
+        return cls._fn.apply(*args)
+
+
+class PairHistLossFn:
+    """loss = mean_k (h_k(x) - target_k)^2 of the box's current positions
+    (which must be x, e.g. the x_T a TrajectoryFn returned)."""
+
+    _fn = None
+
+    @classmethod
+    def apply(cls, *args):
+        if cls._fn is None:
+            torch = _torch()
+
+            class _F(torch.autograd.Function):
+                @staticmethod
+                def forward(ctx, x, box, target, nbins, rhist, width, rmax):
+                    h, _ = box.pair_hist(nbins, rhist, width, rmax)
+                    t = target.detach().cpu().numpy().reshape(1, -1)
+                    diff = h - t
+                    ctx.box, ctx.args, ctx.diff = box, (nbins, rhist, width, rmax), diff
+                    return torch.tensor(float(np.mean(diff * diff)), dtype=torch.float64,
+                                        device=x.device)
+
+                @staticmethod
+                def backward(ctx, g):
+                    nbins, rhist, width, rmax = ctx.args
+                    coef = 2.0 * ctx.diff / nbins * float(g)
+                    _, grad = ctx.box.pair_hist(nbins, rhist, width, rmax, coef=coef)
+                    return (torch.from_numpy(grad).to(g.device), None, None, None, None, None, None)
+
+            cls._fn = _F
+        return cls._fn.apply(*args)
