@@ -179,6 +179,75 @@ def timed_integrate(box, dt, steps, thermo_dev):
     return e0.elapsed_time(e1)
 
 
+def timed_call(fn):
+    """Milliseconds of fn() on the device (CUDA events on the current stream;
+    the library orders its work with that stream)."""
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    out = fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), out
+
+
+def bench_adjoint(ljmd, inputs):
+    """Adjoint/forward time ratio on the differentiable workload: N = 32,000
+    (fcc 20^3 x 4), 200 steps, checkpoints every 20, loss = mean squared
+    deviation of the final pair-distance histogram (64 bins on [0, 2.5],
+    Gaussian width = bin width) from a target."""
+    s = inputs.lj32000()
+    nsteps, k = 200, 20
+    b = ljmd.from_system(s, "mixed_ds")
+    target = b.pair_hist(64, 2.5, 2.5 / 64, 2.8)[0][0] * 0.9
+    zeros = np.zeros((s.n, 3))
+    res = {}
+    for rep in range(3):                      # the first round is warm-up
+        b.set_state(s.pos, s.vel)
+        t_plain, _ = timed_call(lambda: b.integrate(s.dt, nsteps, thermo=False))
+        b.set_state(s.pos, s.vel)
+        t_rec, _ = timed_call(lambda: b.integrate(s.dt, nsteps, thermo=False, ckpt_every=k))
+        h = b.pair_hist(64, 2.5, 2.5 / 64, 2.8)[0][0]
+        coef = 2.0 * (h - target) / 64
+        lx_T = b.pair_hist(64, 2.5, 2.5 / 64, 2.8, coef=coef)[1]
+        t_adj, out = timed_call(lambda: b.adjoint(lx_T, zeros))
+        if rep:
+            for key, v in (("forward_ms", t_plain), ("recorded_forward_ms", t_rec), ("adjoint_ms", t_adj)):
+                res.setdefault(key, []).append(v)
+    med = {key: float(np.median(v)) for key, v in res.items()}
+    b.close()
+    return {"workload": "fcc 20^3 x 4 = 32,000 particles, rho 0.8442, T 0.722, 200 steps, "
+                        "checkpoints every 20, pair-histogram loss (64 bins)",
+            "forward_ms": med["forward_ms"], "recorded_forward_ms": med["recorded_forward_ms"],
+            "adjoint_ms": med["adjoint_ms"],
+            "ratio": med["adjoint_ms"] / med["forward_ms"],
+            "ratio_vs_recorded_forward": med["adjoint_ms"] / med["recorded_forward_ms"],
+            "dL_deps": float(out[2][0, 0]), "dL_dsigma": float(out[3][0, 0])}
+
+
+def bench_batched(ljmd, inputs, steps):
+    """512 independent boxes, N log-uniform in [500, 20000], rho U[0.6, 0.95],
+    T U[0.7, 1.5], advanced together (one launch per phase, graph-captured)."""
+    systems = inputs.replica_systems(512, seed=inputs.SEEDS["replicas512"])
+    n = [x.n for x in systems]
+    pos = np.concatenate([x.pos for x in systems])
+    vel = np.concatenate([x.vel for x in systems])
+    box = np.stack([x.box for x in systems])
+    b = ljmd.Box(pos, box, vel, n=n, precision="mixed_ds")
+    b.set_lj(1.0, 1.0, 2.5, 0.3)
+    import torch
+    th = torch.zeros((steps, 512, 4), dtype=torch.float64, device="cuda")
+    b.integrate(0.005, 20, thermo=True, out=th[:20])
+    ms, _ = timed_call(lambda: b.integrate(0.005, steps, thermo=True, out=th))
+    tot = int(sum(n))
+    b.close()
+    return {"workload": "512 replicas, N log-uniform [500, 20000], rho U[0.6, 0.95], T U[0.7, 1.5], "
+                        "dt 0.005", "particles": tot, "steps": steps, "ms_per_step": ms / steps,
+            "value": tot * steps / (ms / 1e3), "unit": UNIT}
+
+
 def run_gpu(args):
     import torch
     from paper_2406_04210_gb300 import build, inputs, ljmd
@@ -269,6 +338,9 @@ def run_gpu(args):
         prec[p] = n * k / (ms2 / 1e3)
         b2.close()
 
+    adj = None if args.quick else bench_adjoint(ljmd, inputs)
+    batched = None if args.quick else bench_batched(ljmd, inputs, max(50, args.steps // 5))
+
     if rank != 0:
         if dist:
             dist.barrier()
@@ -297,7 +369,8 @@ def run_gpu(args):
         "energy": {"E_per_particle_first": float(E[0] / n), "E_per_particle_last": float(E[-1] / n),
                    "drift_per_particle": float((E[-1] - E[0]) / n)},
         "rebuilds_in_timed_region": int(info1.rebuilds - info0.rebuilds),
-        "adjoint_forward_ratio": None,
+        "adjoint_forward_ratio": adj["ratio"] if adj else None,
+        "adjoint": adj, "batched": batched,
     }
     print(json.dumps(line), flush=True)
     if dist:
