@@ -298,12 +298,15 @@ __device__ __forceinline__ bool exact_within(const BoxDev& b, const RepDev& R, i
     return d2 < b.rl2;
 }
 
-__global__ void __launch_bounds__(LJ_LIST_THREADS) k_nlist(BoxDev b)
+__global__ void __launch_bounds__(LJ_LIST_THREADS, 3) k_nlist(BoxDev b)
 {
     if (!box_needs_rebuild(b)) return;
-    __shared__ __align__(16) float4 s_tile[LJ_TILE_MAX];
+    extern __shared__ __align__(16) float4 s_tile[];   // LJ_TILE_MAX entries
     __shared__ float4 s_shift[32];
     __shared__ int4 s_rng[LJ_SEG_MAX_CELLS * 27];   // (first, end, tile offset) per (cell, k)
+    __shared__ int s_qoff[LJ_SEG_MAX_CELLS + 1];     // first quad of each cell
+    __shared__ uint16_t s_flat[(LJ_LIST_THREADS / 32) * LJ_FLAT_MAX];   // per-warp candidate list
+    __shared__ int s_koff[(LJ_LIST_THREADS / 32) * 32];                  // per-warp tile offsets
     __shared__ Tile s_t;
     __shared__ __align__(8) unsigned long long s_bar;
     if (threadIdx.x == 0) mbar_init(&s_bar, 1);
@@ -311,9 +314,6 @@ __global__ void __launch_bounds__(LJ_LIST_THREADS) k_nlist(BoxDev b)
     int cur_r = -1;
     const float lo2 = b.rl2f - b.band, hi2 = b.rl2f + b.band;
     // LJ_TPP threads per particle: lanes l8 of group grp share the particle
-    const int grp = threadIdx.x / LJ_TPP, l8 = threadIdx.x % LJ_TPP;
-    const int gshift = (threadIdx.x & 31) & ~(LJ_TPP - 1);
-    const unsigned gmask = ((1u << LJ_TPP) - 1u) << gshift;
     for (int w = blockIdx.x; w < b.nseg; w += gridDim.x) {
         int4 sg = b.seg[w];
         int r = sg.x;
@@ -354,50 +354,113 @@ __global__ void __launch_bounds__(LJ_LIST_THREADS) k_nlist(BoxDev b)
         if (s_t.total > 0 && !stage_tile_bulk(b.posq, s_t, s_tile, &s_bar, phase, b.err)) return;
         const float ell_h[3] = {0.5f * R.ellf[0], 0.5f * R.ellf[1], 0.5f * R.ellf[2]};
         const float rcull = b.rl2f + b.band;
-        for (int base = 0; base < n; base += LJ_LIST_THREADS / LJ_TPP) {
-            const int il = base + grp;
-            if (il >= n) continue;                // group-uniform
-            const int p = p0 + il;
-            const float4 pi = b.posq[p];
-            const int4* rng = s_rng + (b.cell[p] - c0) * 27;
-            uint32_t* out = b.nbr + (size_t)b.K * p;
-            int cnt = 0;
-            for (int k = 0; k < 27; ++k) {
-                const int4 rk = rng[k];
-                const int js = rk.x, je = rk.y, toff = rk.z;
-                if (js == je) continue;
-                // skip the cell if its box lies beyond the list radius
-                const float4 sh = s_shift[k];
-                const float gx = fmaxf(fabsf(pi.x - sh.x) - ell_h[0], 0.f);
-                const float gy = fmaxf(fabsf(pi.y - sh.y) - ell_h[1], 0.f);
-                const float gz = fmaxf(fabsf(pi.z - sh.z) - ell_h[2], 0.f);
-                if (gx * gx + gy * gy + gz * gz >= rcull) continue;
-                for (int jb = js; jb < je; jb += LJ_TPP) {
-                    const int j = jb + l8;
-                    bool in = false;
-                    if (j < je && !(j == p && k == 13)) {
-                        const float4 pj = s_tile[j + toff];
-                        const float ddx = (pi.x - pj.x) - sh.x;
-                        const float ddy = (pi.y - pj.y) - sh.y;
-                        const float ddz = (pi.z - pj.z) - sh.z;
+        // work units: quads of particles of one cell (the 4 groups of a warp
+        // share the cell, so their candidate loops are identical)
+        if (threadIdx.x == 0) {
+            int q = 0;
+            for (int cl = 0; cl < sg.w; ++cl) {
+                s_qoff[cl] = q;
+                q += (b.cell_end[c0 + cl] - b.cell_start[c0 + cl] + 3) >> 2;
+            }
+            s_qoff[sg.w] = q;
+        }
+        __syncthreads();
+        const int nquad = s_qoff[sg.w];
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        uint16_t* flat = s_flat + warp * LJ_FLAT_MAX;
+        int* koff = s_koff + warp * 32;
+        for (int qd = warp; qd < nquad; qd += LJ_LIST_THREADS / 32) {
+            int cl = 0;
+            while (s_qoff[cl + 1] <= qd) ++cl;                  // warp-uniform
+            const int cs = b.cell_start[c0 + cl], ce = b.cell_end[c0 + cl];
+            const int p0q = cs + 4 * (qd - s_qoff[cl]);          // first particle of the quad
+            const int nq = min(4, ce - p0q);                     // particles in the quad
+            // the quad's particles, in every lane's registers
+            float4 pq[4];
+#pragma unroll
+            for (int g = 0; g < 4; ++g) pq[g] = b.posq[p0q + (g < nq ? g : 0)];
+            const int4* rng = s_rng + cl * 27;
+            // flatten the candidate cells (lane k owns stencil cell k); a cell
+            // is dropped when its box lies beyond the list radius of all the
+            // quad's particles
+            int len = 0;
+            int4 rk = make_int4(0, 0, 0, 0);
+            if (lane < 27) {
+                rk = rng[lane];
+                const float4 sh = s_shift[lane];
+                bool far = true;
+#pragma unroll
+                for (int g = 0; g < 4; ++g) {
+                    const float gx = fmaxf(fabsf(pq[g].x - sh.x) - ell_h[0], 0.f);
+                    const float gy = fmaxf(fabsf(pq[g].y - sh.y) - ell_h[1], 0.f);
+                    const float gz = fmaxf(fabsf(pq[g].z - sh.z) - ell_h[2], 0.f);
+                    far = far && (g >= nq || gx * gx + gy * gy + gz * gz >= rcull);
+                }
+                len = far ? 0 : rk.y - rk.x;
+            }
+            int incl = len;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            if (lane < 27) koff[lane] = rk.z;   // tile offset of cell k
+            const int off = incl - len;
+            int cnt[4] = {0, 0, 0, 0};
+            const unsigned lt_mask = (1u << lane) - 1u;
+            for (int w0 = 0; w0 < total; w0 += LJ_FLAT_MAX) {
+                const int wn = min(total - w0, LJ_FLAT_MAX);
+                __syncwarp();
+                for (int k = 0; k < 27; ++k) {
+                    const int lk = __shfl_sync(0xffffffffu, len, k);
+                    const int ok = __shfl_sync(0xffffffffu, off, k) - w0;
+                    const int ik = __shfl_sync(0xffffffffu, rk.x + rk.z, k);   // first tile index
+                    const int t_lo = max(0, -ok), t_hi = min(lk, wn - ok);
+                    for (int t = t_lo + lane; t < t_hi; t += 32)
+                        flat[ok + t] = (uint16_t)((k << LJ_TILE_BITS) | (ik + t));
+                }
+                __syncwarp();
+                // one candidate per lane, tested against the quad's particles
+                for (int t0 = 0; t0 < wn; t0 += 32) {
+                    const int t = t0 + lane;
+                    const bool valid = t < wn;
+                    const unsigned e = valid ? flat[t] : 0u;
+                    const int k = (int)(e >> LJ_TILE_BITS);
+                    const int idx = (int)(e & LJ_TILE_MASK);
+                    const float4 pj = s_tile[idx];
+                    const float4 sh = s_shift[k];
+                    const float qx = pj.x + sh.x, qy = pj.y + sh.y, qz = pj.z + sh.z;
+                    const int j = idx - koff[k];
+                    const uint32_t ent = ((uint32_t)k << LJ_IDX_BITS) | (uint32_t)j;
+#pragma unroll
+                    for (int g = 0; g < 4; ++g) {
+                        if (g >= nq) break;                           // warp-uniform
+                        const float ddx = pq[g].x - qx, ddy = pq[g].y - qy, ddz = pq[g].z - qz;
                         const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                        if (r2 < lo2) in = true;
-                        else if (r2 < hi2) in = exact_within(b, R, p, j);
+                        const bool cand = valid && !(j == p0q + g && k == 13);
+                        bool in = cand && r2 < lo2;
+                        const bool band = cand && !in && r2 < hi2;
+                        if (__any_sync(0xffffffffu, band)) {          // rare: FP64 recheck near rl
+                            if (band) in = exact_within(b, R, p0q + g, j);
+                        }
+                        const unsigned bits = __ballot_sync(0xffffffffu, in);
+                        if (in) {
+                            const int pos = cnt[g] + __popc(bits & lt_mask);
+                            if (pos < b.K) b.nbr[(size_t)b.K * (p0q + g) + pos] = ent;
+                        }
+                        cnt[g] += __popc(bits);
                     }
-                    const unsigned bits = (__ballot_sync(gmask, in) >> gshift) & ((1u << LJ_TPP) - 1u);
-                    if (in) {
-                        const int pos = cnt + __popc(bits & ((1u << l8) - 1u));
-                        if (pos < b.K) out[pos] = ((uint32_t)k << LJ_IDX_BITS) | (uint32_t)j;
-                    }
-                    cnt += __popc(bits);
                 }
             }
-            if (l8 == 0) {
-                b.nbr_count[p] = cnt;
-                atomicMax(&b.err[2], cnt);   // longest list of this build
-                if (cnt > b.K) {
+            if (lane < nq) {
+                const int c = lane == 0 ? cnt[0] : lane == 1 ? cnt[1] : lane == 2 ? cnt[2] : cnt[3];
+                const int p = p0q + lane;
+                b.nbr_count[p] = c;
+                atomicMax(&b.err[2], c);   // longest list of this build
+                if (c > b.K) {
                     atomicOr(&b.err[0], LJ_ERRBIT_CAPACITY);
-                    atomicMax(&b.err[1], cnt);
+                    atomicMax(&b.err[1], c);
                 }
             }
         }
@@ -436,7 +499,14 @@ cudaError_t launch_sortgather(const BoxDev& b, Launch l)
 
 cudaError_t launch_nlist(const BoxDev& b, Launch l)
 {
-    k_nlist<<<l.grid, LJ_LIST_THREADS, 0, l.s>>>(b);
+    const int dyn = LJ_TILE_MAX * 16;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_nlist, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_nlist<<<l.grid, LJ_LIST_THREADS, dyn, l.s>>>(b);
     return cudaGetLastError();
 }
 

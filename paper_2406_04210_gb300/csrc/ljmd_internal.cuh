@@ -42,6 +42,7 @@
 #define LJ_F64_THREADS 128     // threads of the FP64 pair kernel (one per particle)
 #define LJ_TPP 8               // threads per particle in the pair kernels
 #define LJ_SEG_MAX_CELLS 16    // most cells in one segment
+#define LJ_FLAT_MAX 1024       // candidates of one cell's 27-cell neighbourhood (list build)
 #define LJ_LIST_SMEM (32 * 1024)   // bytes of a segment's list staged in smem
 
 // error word bits (err[0]); err[1] = largest list length beyond capacity;
