@@ -360,7 +360,8 @@ def run_gpu(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 forces / double-single state",
         "data": "synthetic", "config": dict(WORKLOAD, parallelism=f"replicas{world}"),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": TRAFFIC_PER_LAUNCH,
+                     "frac": achieved / peak,
+                     "traffic": (DRAM_BYTES_PER_PARTICLE * n) if DRAM_BYTES_PER_PARTICLE else None,
                      "kernel": "k_force_f32 (pair force, energy+virial)",
                      "bytes_per_launch": force_bytes, "avg_launch_ms": f_avg,
                      "peak_kind": f"hbm_gbs of {peak_kind} peaks (copy, burst)"},
@@ -378,9 +379,11 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-#: dram read+write bytes per force launch from the committed ncu summary of
-#: the current kernel (profiles/k_force_f32_lj4m.md); None when not measured
-TRAFFIC_PER_LAUNCH = None
+#: DRAM read + write bytes per particle of one k_force_f32 launch (energy
+#: variant), from the ncu capture summarised in profiles/k_force_f32_lj256k.md
+#: (256,000 particles, scaled by the particle count); None when the kernel has
+#: changed since.
+DRAM_BYTES_PER_PARTICLE = 416.2
 
 
 def main():
