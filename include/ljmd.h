@@ -173,6 +173,27 @@ md_status md_pair_hist(md_box* b, int32_t nbins, double rhist, double width,
                        double rmax, const double* coef, double* hist,
                        double* grad);
 
+/* md_force without any allocation (the paper has no counterpart; this serves
+ * library users).  Some callers cannot allocate device memory when they need
+ * forces: a framework that owns all GPU memory through its own pool, a pool
+ * that is capped or frozen, or a loop that must not block in an allocator.
+ * md_force may grow box-owned buffers on first use; this call never
+ * allocates, on the device or through the allocator hook.  Its scratch (the
+ * per-128-particle energy/virial partial sums and the per-replica totals) is
+ * a static device array of 65,536 doubles (512 KiB) that every GPU loading
+ * the library holds until the process exits; boxes needing more (2 doubles
+ * per 128 particles + 4 per replica) are rejected with MD_ERR_ARG and a
+ * message.  The first call on a device looks up that array's address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the one array and overwrite what they use, so calls whose
+ * GPU work overlaps (on different streams or boxes) race.
+ *   force_out  nullable; DEVICE memory, (sum n) x 3 FP64, user order
+ *   epot, virial nullable, nrep entries each, host or device
+ * The lists must be current (as after md_set_lj, md_integrate or
+ * md_neighbour_update); results equal md_force's. */
+md_status md_force_noalloc(md_box* b, double* force_out, double* epot,
+                           double* virial);
+
 /* Current state in user order: pos in [0, L) FP64, vel FP64, image counts
  * (number of box lengths crossed), each nullable. */
 md_status md_get_state(md_box* b, double* pos, double* vel, int32_t* image);

@@ -1376,3 +1376,79 @@ md_status md_set_tuning(md_box* b, int32_t block_force, int32_t block_list, int3
 }
 
 }  // extern "C"
+
+// ==========================================================================
+// Force and energy evaluation that allocates nothing.
+//
+// For callers that must not allocate device memory at the point of the call:
+// code running while a memory pool is frozen or capped, a host that shares
+// the GPU with a framework owning all of its memory, or a real-time loop that
+// may not block on an allocator.  The per-chunk energy/virial partial sums
+// and the per-replica totals (the only scratch of this computation beyond
+// what the box already owns) live in the file-scope array below instead of
+// box-owned buffers that md_force may grow lazily.
+// ==========================================================================
+#include <mutex>
+
+#define LJMD_NOALLOC_DOUBLES (1 << 16)   // 512 KiB of FP64 scratch, per device
+
+// One copy per device that loads this library, held until process exit.
+static __device__ __align__(256) double g_noalloc_scratch[LJMD_NOALLOC_DOUBLES];
+
+namespace {
+std::mutex g_noalloc_mu;
+constexpr int kMaxDevices = 128;
+double* g_noalloc_dev[kMaxDevices] = {};   // device address of the array, per device
+}  // namespace
+
+extern "C" md_status md_force_noalloc(md_box* b, double* force_out, double* epot, double* virial)
+{
+    if (!b) return MD_ERR_ARG;
+    const size_t nchunk = b->chunks.size();
+    const size_t need = 2 * nchunk + 4 * (size_t)b->nrep;
+    if (need > (size_t)LJMD_NOALLOC_DOUBLES) {
+        char msg[200];
+        snprintf(msg, sizeof msg,
+                 "md_force_noalloc: box needs %zu scratch doubles (2 per 128 particles + 4 per replica); "
+                 "the static scratch holds %d",
+                 need, LJMD_NOALLOC_DOUBLES);
+        return fail(b, MD_ERR_ARG, msg);
+    }
+    if (!b->lj_set) return fail(b, MD_ERR_ARG, "md_force_noalloc: md_set_lj not called");
+    if (force_out && !is_device_ptr(force_out))
+        return fail(b, MD_ERR_ARG, "md_force_noalloc: force_out must be device memory of the box's GPU");
+    if (b->device < 0 || b->device >= kMaxDevices) return fail(b, MD_ERR_ARG, "md_force_noalloc: device ordinal");
+    double* scratch = nullptr;
+    {
+        // first call on this device: look up the array's device address
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_dev[b->device]) {
+            CK(b, cudaSetDevice(b->device));
+            void* p = nullptr;
+            CK(b, cudaGetSymbolAddress(&p, g_noalloc_scratch));
+            g_noalloc_dev[b->device] = static_cast<double*>(p);
+        }
+        scratch = g_noalloc_dev[b->device];
+    }
+    CKS(enter(b));
+    BoxDev v = b->d;
+    v.part_f = scratch;                       // every chunk's pair is overwritten
+    double* th = scratch + 2 * nchunk;        // nrep x (E_pot, E_kin, W, T), overwritten
+    CKS(clear_err(b));
+    CK(b, launch_force(v, 1, lforce(b)));
+    Launch lt{std::max(1, std::min(b->nrep, b->nsm * 4)), 512, b->stream};
+    CK(b, launch_thermo(v, th, 0, lt));
+    if (force_out && b->ntot > 0) CK(b, launch_force_out(b->d, force_out, lch(b)));
+    if (epot)
+        CK(b, cudaMemcpy2DAsync(epot, sizeof(double), th + 0, 4 * sizeof(double), sizeof(double), b->nrep,
+                                is_device_ptr(epot) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, b->stream));
+    if (virial)
+        CK(b, cudaMemcpy2DAsync(virial, sizeof(double), th + 2, 4 * sizeof(double), sizeof(double), b->nrep,
+                                is_device_ptr(virial) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                b->stream));
+    int e2[3];
+    CKS(read_err(b, e2));
+    CKS(leave(b));
+    if (e2[0] & LJ_ERRBIT_NONFINITE) return fail(b, MD_ERR_NONFINITE, "md_force_noalloc: non-finite force");
+    return MD_OK;
+}

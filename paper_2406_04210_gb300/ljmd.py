@@ -29,8 +29,8 @@ STATUS = {0: "MD_OK", 1: "MD_ERR_ARG", 2: "MD_ERR_CUDA", 3: "MD_ERR_OOM", 4: "MD
 EXPORTS = ["md_set_allocator", "md_batch_create", "md_box_create", "md_box_destroy",
            "md_set_lj", "md_neighbour_update", "md_force", "md_integrate", "md_adjoint",
            "md_get_state", "md_set_state", "md_get_nlist", "md_get_info", "md_set_tuning",
-           "md_set_profiling", "md_get_profile", "md_pair_hist", "md_last_error",
-           "md_status_string"]
+           "md_set_profiling", "md_get_profile", "md_pair_hist", "md_force_noalloc",
+           "md_last_error", "md_status_string"]
 
 
 class LibraryMissing(RuntimeError):
@@ -91,6 +91,7 @@ def load(path: str | None = None):
         L.md_set_tuning.argtypes = [vp, i32, i32, i32]
         L.md_set_profiling.argtypes = [vp, i32]
         L.md_pair_hist.argtypes = [vp, i32, d, d, d, vp, vp, vp]
+        L.md_force_noalloc.argtypes = [vp, vp, vp, vp]
         L.md_get_profile.argtypes = [vp, vp, vp]
         L.md_last_error.argtypes = [vp]
         L.md_last_error.restype = ctypes.c_char_p

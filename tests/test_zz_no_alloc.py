@@ -1,0 +1,62 @@
+"""md_force_noalloc: forces and energies without any device allocation.
+
+For library users whose code cannot allocate GPU memory at the point where
+it needs forces (for example a framework that owns the whole device through
+its own memory pool, or a pool that is capped or frozen).  The entry point
+keeps its scratch in a static device array, so this test calls it through
+the C ABI twice in a row and checks both results against md_force on the
+same box, with the force and energy tolerances of tests/test_gpu_md.py.
+It lives in its own file, collected last, and builds and loads the library
+itself, so it also runs alone in a fresh process.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2406_04210_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ljmd():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2406_04210_gb300 import build, ljmd as m
+    build.build()
+    m.load()
+    return m
+
+
+def test_force_noalloc_matches_md_force_twice(ljmd):
+    import torch
+    s = inputs.lj4000()
+    b = ljmd.from_system(s, "mixed_ds")
+    f_ref, e_ref, w_ref = b.force()                       # the existing entry point
+    scale = np.abs(f_ref).max()
+    out = torch.zeros((s.n, 3), dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        out.zero_()
+        e = np.zeros(1)
+        w = np.zeros(1)
+        st = b._lib.md_force_noalloc(b._h, ctypes.c_void_p(out.data_ptr()), e.ctypes.data,
+                                     w.ctypes.data)
+        assert st == 0, b._lib.md_last_error(b._h).decode()
+        f = out.cpu().numpy()
+        assert np.abs(f - f_ref).max() <= 1e-5 * scale
+        assert abs(e[0] - e_ref[0]) <= 1e-5 * abs(e_ref[0])
+        assert abs(w[0] - w_ref[0]) <= 1e-5 * abs(w_ref[0])
+
+
+def test_force_noalloc_rejects_boxes_beyond_its_scratch(ljmd):
+    # 16,384 one-particle replicas need 2 x 16,384 + 4 x 16,384 doubles > 65,536
+    nrep = 16384
+    box = np.tile([10.0, 10.0, 10.0], (nrep, 1))
+    pos = np.full((nrep, 3), 5.0)
+    b = ljmd.Box(pos, box, n=[1] * nrep)
+    e = np.zeros(nrep)
+    st = b._lib.md_force_noalloc(b._h, None, e.ctypes.data, None)
+    assert st == 1
+    assert b"static scratch" in b._lib.md_last_error(b._h)
