@@ -270,6 +270,7 @@ def run_gpu(args):
     s = inputs.fcc_system(args.ncell, seed=inputs.SEEDS["lj4m"] + rank)
     n = s.n
     box = ljmd.from_system(s, "mixed_ds")
+    tuning = box.autotune(reps=3, cache=False)        # launch/layout autotuner
     thermo = torch.zeros((max(args.steps, args.warmup, 1), 1, 4), dtype=torch.float64,
                          device="cuda")
     if args.warmup:
@@ -371,7 +372,7 @@ def run_gpu(args):
                    "drift_per_particle": float((E[-1] - E[0]) / n)},
         "rebuilds_in_timed_region": int(info1.rebuilds - info0.rebuilds),
         "adjoint_forward_ratio": adj["ratio"] if adj else None,
-        "adjoint": adj, "batched": batched,
+        "adjoint": adj, "batched": batched, "tuning": tuning,
     }
     print(json.dumps(line), flush=True)
     if dist:

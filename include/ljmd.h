@@ -227,12 +227,25 @@ typedef struct {
 
 md_status md_get_info(md_box* b, md_info* out);
 
-/* Tuning.  block_force / block_list: reserved (0).  capacity: neighbour-list
- * slots per particle to lay the lists out with now and at later parameter
- * changes (0 = automatic: 1.3 x the mean count at the densest replica + 16).
- * Lists always regrow by themselves when a build needs more slots. */
-md_status md_set_tuning(md_box* b, int32_t block_force, int32_t block_list,
-                        int32_t capacity);
+/* Launch and layout tuning, t[4]:
+ *   t[0] blocks per SM of the pair-force kernels  (0 = default: 6, FP64 12)
+ *   t[1] blocks per SM of the list build          (0 = default: 6)
+ *   t[2] cells per list-build segment, <= 16      (0 = automatic: ~1400
+ *        particles per 27-cell tile)
+ *   t[3] neighbour-list slots per particle       (0 = automatic: fitted to
+ *        1.1 x the longest list + 8 after the first build)
+ * Lists always regrow by themselves when a build needs more slots.
+ * md_set_tuning applies t now (rebuilding the lists if t[2] or t[3] asks);
+ * md_get_tuning reads the current values. */
+md_status md_set_tuning(md_box* b, const int32_t t[4]);
+md_status md_get_tuning(md_box* b, int32_t t[4]);
+
+/* Autotuner: times `reps` launches of the pair-force kernel for each
+ * blocks-per-SM candidate, and `reps` forced list builds for each segment
+ * length (automatic choice +-2) x list blocks-per-SM candidate, at the
+ * current positions; applies the fastest and returns it in t[4] (as
+ * md_get_tuning).  The box's state is unchanged apart from a list rebuild. */
+md_status md_autotune(md_box* b, int32_t reps, int32_t t[4]);
 
 /* Phase timing of md_integrate.  md_set_profiling(b, 1) resets the counters
  * and makes later md_integrate calls record CUDA events around each phase of

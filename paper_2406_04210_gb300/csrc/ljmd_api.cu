@@ -100,6 +100,9 @@ struct md_box {
     // tuning
     int min_capacity = 0;
     bool autofit = false;      // fit the capacity after the next full build
+    int force_per_sm = 0;      // 0 = automatic (tuning)
+    int list_per_sm = 0;
+    int seg_cells = 0;
     int64_t steps = 0;
     int64_t launches = 0;
     bool profiling = false;
@@ -231,10 +234,14 @@ Launch lcell(md_box* b) { return Launch{std::max(1, std::min((b->d.ncell + 7) / 
 Launch lseg(md_box* b) { return Launch{std::max(1, std::min(b->d.nseg, b->nsm * 8)), LJ_SEG_THREADS, b->stream}; }
 Launch lforce(md_box* b)
 {
-    int per_sm = b->prec == 2 ? 12 : 6;
+    int per_sm = b->force_per_sm > 0 ? b->force_per_sm : (b->prec == 2 ? 12 : 6);
     return Launch{std::max(1, std::min((int)b->d.nchunk, b->nsm * per_sm)), 0, b->stream};
 }
-Launch llist(md_box* b) { return Launch{std::max(1, std::min(b->d.nseg, b->nsm * 6)), LJ_LIST_THREADS, b->stream}; }
+Launch llist(md_box* b)
+{
+    int per_sm = b->list_per_sm > 0 ? b->list_per_sm : 6;
+    return Launch{std::max(1, std::min(b->d.nseg, b->nsm * per_sm)), LJ_LIST_THREADS, b->stream};
+}
 
 // Fence: internal stream waits for the caller's stream.
 md_status enter(md_box* b)
@@ -345,6 +352,8 @@ md_status make_segments(md_box* b, bool shrink)
         RepDev& R = b->reps[r];
         if (shrink) {
             R.S = std::max(1, R.S / 2);
+        } else if (b->seg_cells > 0) {
+            R.S = std::max(1, std::min(std::min(b->seg_cells, R.nc[0]), LJ_SEG_MAX_CELLS));
         } else {
             double per_cell = R.ncell > 0 ? (double)R.n / R.ncell : 0.0;
             int S = per_cell > 0 ? (int)std::floor(1400.0 / (9.0 * per_cell)) - 2 : R.nc[0];
@@ -622,6 +631,26 @@ void copy_reps_to(md_box* b, BoxDev& d)
     d.np = b->np;
     d.nchunk = (int)b->chunks.size();
     d.prec = b->prec;
+}
+
+// Time `reps` launches of fn on the box stream (milliseconds per launch).
+template <class F>
+md_status time_launches(md_box* b, int reps, F fn, float* ms_out)
+{
+    cudaEvent_t e0, e1;
+    CK(b, cudaEventCreate(&e0));
+    CK(b, cudaEventCreate(&e1));
+    CKS(fn());   // warm-up
+    CK(b, cudaEventRecord(e0, b->stream));
+    for (int i = 0; i < reps; ++i) CKS(fn());
+    CK(b, cudaEventRecord(e1, b->stream));
+    CK(b, cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(b, cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms_out = ms / (float)std::max(1, reps);
+    return MD_OK;
 }
 
 }  // namespace
@@ -1359,20 +1388,91 @@ md_status md_get_profile(md_box* b, double* ms, int64_t* launches)
     return MD_OK;
 }
 
-md_status md_set_tuning(md_box* b, int32_t block_force, int32_t block_list, int32_t capacity)
+md_status md_get_tuning(md_box* b, int32_t t[4])
 {
-    if (!b || capacity < 0) return MD_ERR_ARG;
-    (void)block_force;
-    (void)block_list;
-    b->min_capacity = capacity;
-    if (capacity > 0 && b->lj_set) {
-        // re-layout the lists at this capacity now (they regrow on overflow)
+    if (!b || !t) return MD_ERR_ARG;
+    t[0] = b->force_per_sm;
+    t[1] = b->list_per_sm;
+    t[2] = b->seg_cells;
+    t[3] = b->min_capacity;
+    return MD_OK;
+}
+
+md_status md_set_tuning(md_box* b, const int32_t t[4])
+{
+    if (!b || !t || t[0] < 0 || t[0] > 32 || t[1] < 0 || t[1] > 32 || t[2] < 0 || t[2] > LJ_SEG_MAX_CELLS ||
+        t[3] < 0)
+        return fail(b, MD_ERR_ARG, "md_set_tuning: values out of range");
+    const bool seg_changed = t[2] != b->seg_cells;
+    b->force_per_sm = t[0];
+    b->list_per_sm = t[1];
+    b->seg_cells = t[2];
+    b->min_capacity = t[3];
+    invalidate_graphs(b);
+    if (!b->lj_set) return MD_OK;
+    if (t[3] > 0 || seg_changed) {
         CKS(enter(b));
-        CKS(alloc_lists(b, round_up(capacity, 8)));   // 16-byte list rows
+        if (seg_changed) CKS(make_segments(b, false));
+        if (t[3] > 0) CKS(alloc_lists(b, round_up(t[3], 8)));   // 16-byte list rows
         CKS(full_rebuild(b));
         CKS(leave(b));
     }
     return MD_OK;
+}
+
+md_status md_autotune(md_box* b, int32_t reps, int32_t t[4])
+{
+    if (!b || !b->lj_set || reps < 1) return fail(b, MD_ERR_ARG, "md_autotune: md_set_lj not called");
+    CKS(enter(b));
+    // pair-force grid: blocks per SM
+    const int fcand[] = {2, 3, 4, 6, 8, 12, 16, 24, 32};
+    int best_f = 6;
+    float best_ft = 1e30f;
+    for (int c : fcand) {
+        b->force_per_sm = c;
+        float ms;
+        CKS(time_launches(b, reps, [&]() -> md_status { return enqueue_force(b, 1, nullptr); }, &ms));
+        if (ms < best_ft) {
+            best_ft = ms;
+            best_f = c;
+        }
+    }
+    b->force_per_sm = best_f;
+    // list build: segment length x blocks per SM, timed as forced rebuilds
+    int s0 = b->reps.empty() ? 4 : b->reps[0].S;
+    int best_s = s0, best_l = 6;
+    float best_lt = 1e30f;
+    const int lcand[] = {3, 4, 6, 8, 12};
+    for (int S = std::max(1, s0 - 2); S <= std::min(LJ_SEG_MAX_CELLS, s0 + 2); ++S) {
+        b->seg_cells = S;
+        CKS(make_segments(b, false));
+        for (int lc : lcand) {
+            b->list_per_sm = lc;
+            float ms;
+            md_status st = time_launches(b, reps, [&]() -> md_status {
+                CKS(set_all_rebuild(b));
+                return enqueue_rebuild(b, b->fresh_abs ? 1 : 0);
+            }, &ms);
+            if (st != MD_OK) return st;
+            int e2[3];
+            CKS(read_err(b, e2));
+            if (e2[0] & (LJ_ERRBIT_TILE | LJ_ERRBIT_CAPACITY)) {
+                CKS(clear_err(b));
+                continue;   // this segment length overflows a tile: not a candidate
+            }
+            if (ms < best_lt) {
+                best_lt = ms;
+                best_s = S;
+                best_l = lc;
+            }
+        }
+    }
+    b->seg_cells = best_s;
+    b->list_per_sm = best_l;
+    CKS(make_segments(b, false));
+    CKS(full_rebuild(b));
+    CKS(leave(b));
+    return md_get_tuning(b, t);
 }
 
 }  // extern "C"

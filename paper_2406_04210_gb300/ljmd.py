@@ -29,6 +29,7 @@ STATUS = {0: "MD_OK", 1: "MD_ERR_ARG", 2: "MD_ERR_CUDA", 3: "MD_ERR_OOM", 4: "MD
 EXPORTS = ["md_set_allocator", "md_batch_create", "md_box_create", "md_box_destroy",
            "md_set_lj", "md_neighbour_update", "md_force", "md_integrate", "md_adjoint",
            "md_get_state", "md_set_state", "md_get_nlist", "md_get_info", "md_set_tuning",
+           "md_get_tuning", "md_autotune",
            "md_set_profiling", "md_get_profile", "md_pair_hist", "md_force_noalloc",
            "md_last_error", "md_status_string"]
 
@@ -88,7 +89,9 @@ def load(path: str | None = None):
         L.md_set_state.argtypes = [vp, vp, vp]
         L.md_get_nlist.argtypes = [vp, vp, vp, i64, vp]
         L.md_get_info.argtypes = [vp, ctypes.POINTER(Info)]
-        L.md_set_tuning.argtypes = [vp, i32, i32, i32]
+        L.md_set_tuning.argtypes = [vp, vp]
+        L.md_get_tuning.argtypes = [vp, vp]
+        L.md_autotune.argtypes = [vp, i32, vp]
         L.md_set_profiling.argtypes = [vp, i32]
         L.md_pair_hist.argtypes = [vp, i32, d, d, d, vp, vp, vp]
         L.md_force_noalloc.argtypes = [vp, vp, vp, vp]
@@ -293,9 +296,67 @@ class Box:
         self._check(self._lib.md_get_info(self._h, ctypes.byref(i)), "md_get_info")
         return i
 
-    def set_tuning(self, block_force=0, block_list=0, capacity=0):
-        self._check(self._lib.md_set_tuning(self._h, block_force, block_list, capacity),
-                    "md_set_tuning")
+    TUNING = ("force_blocks_per_sm", "list_blocks_per_sm", "segment_cells", "capacity")
+
+    def tuning(self):
+        t = np.zeros(4, dtype=np.int32)
+        self._check(self._lib.md_get_tuning(self._h, t.ctypes.data), "md_get_tuning")
+        return dict(zip(self.TUNING, (int(x) for x in t)))
+
+    def set_tuning(self, **kw):
+        """Set any of force_blocks_per_sm, list_blocks_per_sm, segment_cells,
+        capacity (0 = automatic); the others keep their current values."""
+        cur = self.tuning()
+        unknown = set(kw) - set(self.TUNING)
+        if unknown:
+            raise TypeError(f"unknown tuning keys {sorted(unknown)}")
+        cur.update(kw)
+        t = np.array([cur[k] for k in self.TUNING], dtype=np.int32)
+        self._check(self._lib.md_set_tuning(self._h, t.ctypes.data), "md_set_tuning")
+
+    def autotune(self, reps=5, cache=True):
+        """Measure and apply the fastest launch/layout settings (md_autotune).
+        With cache, results are kept per (GPU, replicas, log2 N, density) in
+        $XDG_CACHE_HOME/paper_2406_04210_gb300/autotune.json (default
+        ~/.cache/...) and reused instead of re-measuring."""
+        import json
+        key = None
+        path = None
+        if cache:
+            try:
+                import torch
+                gpu = torch.cuda.get_device_name()
+            except Exception:
+                gpu = "cuda"
+            vol = float(np.prod(self.box, axis=1).sum())
+            key = f"{gpu}|{self.precision}|{self.nrep}|{int(np.log2(max(self.n_total, 1)))}|{self.n_total / vol:.2f}"
+            base = os.environ.get("XDG_CACHE_HOME", os.path.join(os.path.expanduser("~"), ".cache"))
+            path = os.path.join(base, "paper_2406_04210_gb300", "autotune.json")
+            try:
+                with open(path) as f:
+                    table = json.load(f)
+            except Exception:
+                table = {}
+            if key in table:
+                self.set_tuning(**table[key])
+                return table[key]
+        t = np.zeros(4, dtype=np.int32)
+        self._check(self._lib.md_autotune(self._h, int(reps), t.ctypes.data), "md_autotune")
+        res = dict(zip(self.TUNING, (int(x) for x in t)))
+        if cache and path:
+            try:
+                os.makedirs(os.path.dirname(path), exist_ok=True)
+                try:
+                    with open(path) as f:
+                        table = json.load(f)
+                except Exception:
+                    table = {}
+                table[key] = res
+                with open(path, "w") as f:
+                    json.dump(table, f, indent=1)
+            except OSError:
+                pass
+        return res
 
     def set_profiling(self, on=True):
         self._check(self._lib.md_set_profiling(self._h, 1 if on else 0), "md_set_profiling")

@@ -213,7 +213,7 @@ def test_capacity_overflow_recovers(ljmd):
     th_ref = ref.integrate(s.dt, 200)
     b = ljmd.from_system(s, "mixed_ds")
     count, _, _ = b.nlist()
-    b.set_tuning(capacity=int(count.max()))     # exactly full: a later build overflows
+    b.set_tuning(capacity=int((count.max() + 7) // 8 * 8))   # full rows: a later build overflows
     k0 = b.info().capacity
     th = b.integrate(s.dt, 200)
     assert b.info().capacity > k0
@@ -280,3 +280,22 @@ def test_torch_device_arrays(ljmd):
     b.force(out=out)
     fh, _, _ = b.force()
     np.testing.assert_array_equal(out.cpu().numpy(), fh)
+
+
+def test_autotune_keeps_results(ljmd):
+    s = inputs.lj4000()
+    b = ljmd.from_system(s, "mixed_ds")
+    f0, e0, _ = b.force()
+    t = b.autotune(reps=2, cache=False)
+    assert 1 <= t["force_blocks_per_sm"] <= 32 and 1 <= t["list_blocks_per_sm"] <= 32
+    assert 1 <= t["segment_cells"] <= 16
+    f1, e1, _ = b.force()
+    S = pair_scale(s.box, s.pos, _lj(s))
+    assert (np.linalg.norm(f1 - f0, axis=1) / S).max() <= 1e-5
+    check_lists(b, s, 2.8)
+    b.set_tuning(segment_cells=1, force_blocks_per_sm=2)
+    th = b.integrate(s.dt, 10)
+    r = oracle.run(s.box, s.pos, s.vel, _lj(s), s.skin, s.dt, 10)
+    d = b.get_state()[0] - r["pos"]
+    d -= s.box * np.rint(d / s.box)
+    assert np.abs(d).max() <= 1e-4
