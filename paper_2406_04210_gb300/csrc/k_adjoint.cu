@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(LJ_FORCE_THREADS) k_hvp_f32(BoxDev b, const fl
                 const int j = (int)(ent & LJ_IDX_MASK);
                 const float4 pj = __ldg(posq + j);
                 const float4 uj = __ldg(u_slot + j);
-                const float4 sh = s_shift[ent >> LJ_IDX_BITS];
+                const float4 sh = s_shift[entry_k(ent)];
                 const float dx = (pi.x - pj.x) - sh.x;
                 const float dy = (pi.y - pj.y) - sh.y;
                 const float dz = (pi.z - pj.z) - sh.z;
@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(LJ_CHUNK) k_pair_hist(BoxDev b, int nbins, flo
                 const int j = (int)(ent & LJ_IDX_MASK);
                 if (b.uid[j] <= ui) continue;
                 const float4 pj = b.posq[j];
-                const float4 sh = s_shift[ent >> LJ_IDX_BITS];
+                const float4 sh = s_shift[entry_k(ent)];
                 const float dx = (pi.x - pj.x) - sh.x, dy = (pi.y - pj.y) - sh.y, dz = (pi.z - pj.z) - sh.z;
                 const float r2 = dx * dx + dy * dy + dz * dz;
                 if (!(r2 < rmax2)) continue;
@@ -340,7 +340,7 @@ __global__ void __launch_bounds__(LJ_CHUNK) k_pair_hist_grad(BoxDev b, int nbins
             const unsigned ent = L[s];
             const int j = (int)(ent & LJ_IDX_MASK);
             const float4 pj = b.posq[j];
-            const float4 sh = s_shift[ent >> LJ_IDX_BITS];
+            const float4 sh = s_shift[entry_k(ent)];
             const float dx = (pi.x - pj.x) - sh.x, dy = (pi.y - pj.y) - sh.y, dz = (pi.z - pj.z) - sh.z;
             const float r2 = dx * dx + dy * dy + dz * dz;
             if (!(r2 < rmax2)) continue;

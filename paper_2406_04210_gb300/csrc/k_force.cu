@@ -47,16 +47,16 @@ __device__ __forceinline__ void block_sum2(double& a, double& c, double (*s)[32]
 // by the cutoff test, so the threads of a particle never diverge.
 template <bool MONO, bool ENERGY>
 __device__ __forceinline__ void pair_f32(unsigned ent, bool valid, const float4& pi, int ti,
-                                         const float4* __restrict__ posq,
-                                         const float4* s_shift, const float4* s_lj, const float* s_rc2,
+                                         const float4* __restrict__ posq, const float3& ell,
+                                         const float4* s_lj, const float* s_rc2,
                                          const float* s_esh, int nt, const float4& mlj, float mrc2,
                                          float mesh, float& fx, float& fy, float& fz, float& e, float& vir)
 {
     const float4 pj = __ldg(posq + (ent & LJ_IDX_MASK));
-    const float4 sh = s_shift[ent >> LJ_IDX_BITS];
-    const float dx = (pi.x - pj.x) - sh.x;
-    const float dy = (pi.y - pj.y) - sh.y;
-    const float dz = (pi.z - pj.z) - sh.z;
+    // d = (o_i - o_j) - (dx, dy, dz) * ell, one rounding per component
+    const float dx = fmaf(-entry_unit(ent, 26), ell.x, pi.x - pj.x);
+    const float dy = fmaf(-entry_unit(ent, 28), ell.y, pi.y - pj.y);
+    const float dz = fmaf(-entry_unit(ent, 30), ell.z, pi.z - pj.z);
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     float4 c;
     float rc2, esh;
@@ -94,7 +94,6 @@ __device__ __forceinline__ void pair_f32(unsigned ent, bool valid, const float4&
 template <bool MONO, bool ENERGY>
 __global__ void __launch_bounds__(LJ_FORCE_THREADS) k_force_f32(BoxDev b)
 {
-    __shared__ float4 s_shift[32];
     __shared__ float4 s_lj[LJ_MAXT * LJ_MAXT];   // c12, c6, e12, e6
     __shared__ float s_rc2[LJ_MAXT * LJ_MAXT];
     __shared__ float s_esh[LJ_MAXT * LJ_MAXT];
@@ -113,19 +112,13 @@ __global__ void __launch_bounds__(LJ_FORCE_THREADS) k_force_f32(BoxDev b)
     const int grp = threadIdx.x / LJ_TPP, l8 = threadIdx.x % LJ_TPP;
     const float4* __restrict__ posq = b.posq;
     int cur_r = -1;
+    float3 ell = make_float3(0.f, 0.f, 0.f);
     for (int w = blockIdx.x; w < b.nchunk; w += gridDim.x) {
         const int4 ch = b.chunk[w];
         const int r = ch.x;
         if (r != cur_r) {                       // block-uniform
-            __syncthreads();
-            if (threadIdx.x < 32) {
-                const RepDev& R = b.rep[r];
-                const int k = threadIdx.x;
-                s_shift[k] = k < 27 ? make_float4((float)(k % 3 - 1) * R.ellf[0], (float)((k / 3) % 3 - 1) * R.ellf[1],
-                                                  (float)(k / 9 - 1) * R.ellf[2], 0.f)
-                                    : make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-            __syncthreads();
+            const RepDev& R = b.rep[r];
+            ell = make_float3(R.ellf[0], R.ellf[1], R.ellf[2]);
             cur_r = r;
         }
         if (threadIdx.x == 0) {
@@ -150,7 +143,7 @@ __global__ void __launch_bounds__(LJ_FORCE_THREADS) k_force_f32(BoxDev b)
             // lane l8 takes entries l8 + 8i; a block of 8 of them (64 entries
             // of the particle) is loaded at once and the next block is in
             // flight while this one is computed
-            const unsigned self = (13u << LJ_IDX_BITS) | (unsigned)(act ? p : 0);
+            const unsigned self = entry_make(13, act ? p : 0);
             unsigned cur[8], nxt[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
@@ -168,9 +161,9 @@ __global__ void __launch_bounds__(LJ_FORCE_THREADS) k_force_f32(BoxDev b)
 #pragma unroll
                 for (int i = 0; i < 8; i += 2) {
                     const int s = blk * 8 * LJ_TPP + l8 + LJ_TPP * i;
-                    pair_f32<MONO, ENERGY>(cur[i], s < cnt, pi, ti, posq, s_shift, s_lj, s_rc2, s_esh, nt, mlj,
+                    pair_f32<MONO, ENERGY>(cur[i], s < cnt, pi, ti, posq, ell, s_lj, s_rc2, s_esh, nt, mlj,
                                            mrc2, mesh, fx, fy, fz, e, vir);
-                    pair_f32<MONO, ENERGY>(cur[i + 1], s + LJ_TPP < cnt, pi, ti, posq, s_shift, s_lj, s_rc2,
+                    pair_f32<MONO, ENERGY>(cur[i + 1], s + LJ_TPP < cnt, pi, ti, posq, ell, s_lj, s_rc2,
                                            s_esh, nt, mlj, mrc2, mesh, fx2, fy2, fz2, e, vir);
                 }
 #pragma unroll
@@ -245,7 +238,7 @@ __global__ void __launch_bounds__(LJ_F64_THREADS) k_force_f64(BoxDev b)
             for (int s = 0; s < cnt; ++s) {
                 unsigned ent = __ldcs(lp + s);
                 int j = (int)(ent & LJ_IDX_MASK);
-                int k = (int)(ent >> LJ_IDX_BITS);
+                int k = entry_k(ent);
                 double dx = (xi - __ldg(&b.off[j])) - s_sh[0][k];
                 double dy = (yi - __ldg(&b.off[np + j])) - s_sh[1][k];
                 double dz = (zi - __ldg(&b.off[2 * np + j])) - s_sh[2][k];

@@ -432,7 +432,7 @@ __global__ void __launch_bounds__(LJ_LIST_THREADS, 3) k_nlist(BoxDev b)
                     const float4 sh = s_shift[k];
                     const float qx = pj.x + sh.x, qy = pj.y + sh.y, qz = pj.z + sh.z;
                     const int j = idx - koff[k];
-                    const uint32_t ent = ((uint32_t)k << LJ_IDX_BITS) | (uint32_t)j;
+                    const uint32_t ent = entry_make(k, j);
 #pragma unroll
                     for (int g = 0; g < 4; ++g) {
                         if (g >= nq) break;                           // warp-uniform

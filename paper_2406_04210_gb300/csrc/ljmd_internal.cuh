@@ -15,9 +15,12 @@
 //     contiguous slot range, and the 27-cell neighbourhood of all its cells
 //     is the "tile": 9 rows x (S + 2) cells, i.e. at most 18 contiguous slot
 //     ranges ("pieces"), staged in shared memory.
-//   * Verlet lists (Sec. 3) are 32-bit entries (stencil code << 27 | slot j).
-//     The stencil code k = 9(dz+1) + 3(dy+1) + (dx+1) names the image shift
-//     of j's cell relative to i's cell, so d_ij = (o_i - o_j) - shift(k).
+//   * Verlet lists (Sec. 3) are 32-bit entries: the image shift of j's cell
+//     relative to i's cell as three 2-bit digits (dz+1, dy+1, dx+1 in bits
+//     31-30, 29-28, 27-26) and the slot j in bits 25-0, so
+//     d_ij = (o_i - o_j) - (dx, dy, dz) * cell edge, decoded with integer and
+//     FP32 arithmetic (no table).  The stencil code k = 9(dz+1) + 3(dy+1) +
+//     (dx+1) orders the 27 cells.
 //     Entry s of particle p is nbr[p K + s] (K a multiple of 8): the 8 threads
 //     of a particle read 8 consecutive entries (one 32-byte sector) at a time.
 //   * the list build works per segment with the tile staged in shared memory;
@@ -30,7 +33,7 @@
 #include <stdint.h>
 
 #define LJ_MAXT 8
-#define LJ_IDX_BITS 27         // slot indices must stay below 2^27
+#define LJ_IDX_BITS 26         // slot indices must stay below 2^26
 #define LJ_IDX_MASK ((1u << LJ_IDX_BITS) - 1u)
 #define LJ_TILE_BITS 11
 #define LJ_TILE_MAX (1 << LJ_TILE_BITS)
@@ -209,6 +212,23 @@ __device__ __forceinline__ bool rep_needs_rebuild(const BoxDev& b, int r)
 }
 
 __device__ __forceinline__ int wrapi(int x, int n) { return x < 0 ? x + n : (x >= n ? x - n : x); }
+
+// ---- list entries ----
+__host__ __device__ __forceinline__ uint32_t entry_make(int k, int j)
+{
+    return ((uint32_t)(k / 9) << 30) | ((uint32_t)((k / 3) % 3) << 28) | ((uint32_t)(k % 3) << 26) |
+           (uint32_t)j;
+}
+__device__ __forceinline__ int entry_k(uint32_t e)
+{
+    return 9 * (int)(e >> 30) + 3 * (int)((e >> 28) & 3u) + (int)((e >> 26) & 3u);
+}
+// The digit at bit `pos` minus one, as an exact FP32 value in {-1, 0, 1}:
+// 0x4B400000 is 1.5 * 2^23, whose mantissa's low bits take the digit.
+__device__ __forceinline__ float entry_unit(uint32_t e, int pos)
+{
+    return __uint_as_float(0x4B400000u | ((e >> pos) & 3u)) - 12582913.0f;
+}
 
 // ---- bulk asynchronous copies (TMA, non-tensor) into shared memory ----
 // One thread arms an mbarrier with the byte count and issues one
