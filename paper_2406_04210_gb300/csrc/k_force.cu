@@ -46,13 +46,11 @@ __device__ __forceinline__ void block_sum2(double& a, double& c, double (*s)[32]
 // with ENERGY, the pair energy and virial; the term is masked (not branched)
 // by the cutoff test, so the threads of a particle never diverge.
 template <bool MONO, bool ENERGY>
-__device__ __forceinline__ void pair_f32(unsigned ent, bool valid, const float4& pi, int ti,
-                                         const float4* __restrict__ posq, const float3& ell,
-                                         const float4* s_lj, const float* s_rc2,
+__device__ __forceinline__ void pair_f32(unsigned ent, const float4& pj, bool valid, const float4& pi, int ti,
+                                         const float3& ell, const float4* s_lj, const float* s_rc2,
                                          const float* s_esh, int nt, const float4& mlj, float mrc2,
                                          float mesh, float& fx, float& fy, float& fz, float& e, float& vir)
 {
-    const float4 pj = __ldg(posq + (ent & LJ_IDX_MASK));
     // d = (o_i - o_j) - (dx, dy, dz) * ell, one rounding per component
     const float dx = fmaf(-entry_unit(ent, 26), ell.x, pi.x - pj.x);
     const float dy = fmaf(-entry_unit(ent, 28), ell.y, pi.y - pj.y);
@@ -92,7 +90,7 @@ __device__ __forceinline__ void pair_f32(unsigned ent, bool valid, const float4&
 // the neighbours' FP32 offsets through L1 and combine their partial forces
 // with shuffles.  MONO: a single species, parameters in registers.
 template <bool MONO, bool ENERGY>
-__global__ void __launch_bounds__(LJ_FORCE_THREADS) k_force_f32(BoxDev b)
+__global__ void __launch_bounds__(LJ_FORCE_THREADS, 4) k_force_f32(BoxDev b)
 {
     __shared__ float4 s_lj[LJ_MAXT * LJ_MAXT];   // c12, c6, e12, e6
     __shared__ float s_rc2[LJ_MAXT * LJ_MAXT];
@@ -158,12 +156,16 @@ __global__ void __launch_bounds__(LJ_FORCE_THREADS) k_force_f32(BoxDev b)
                     const int s = nb + l8 + LJ_TPP * i;
                     nxt[i] = s < cnt ? __ldcs(L + s) : self;
                 }
+                // the neighbours of the whole block: eight gathers in flight
+                float4 pj[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) pj[i] = __ldg(posq + (cur[i] & LJ_IDX_MASK));
 #pragma unroll
                 for (int i = 0; i < 8; i += 2) {
                     const int s = blk * 8 * LJ_TPP + l8 + LJ_TPP * i;
-                    pair_f32<MONO, ENERGY>(cur[i], s < cnt, pi, ti, posq, ell, s_lj, s_rc2, s_esh, nt, mlj,
+                    pair_f32<MONO, ENERGY>(cur[i], pj[i], s < cnt, pi, ti, ell, s_lj, s_rc2, s_esh, nt, mlj,
                                            mrc2, mesh, fx, fy, fz, e, vir);
-                    pair_f32<MONO, ENERGY>(cur[i + 1], s + LJ_TPP < cnt, pi, ti, posq, ell, s_lj, s_rc2,
+                    pair_f32<MONO, ENERGY>(cur[i + 1], pj[i + 1], s + LJ_TPP < cnt, pi, ti, ell, s_lj, s_rc2,
                                            s_esh, nt, mlj, mrc2, mesh, fx2, fy2, fz2, e, vir);
                 }
 #pragma unroll
