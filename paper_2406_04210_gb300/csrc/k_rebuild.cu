@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(LJ_LIST_THREADS, 3) k_nlist(BoxDev b)
     __shared__ int4 s_rng[LJ_SEG_MAX_CELLS * 27];   // (first, end, tile offset) per (cell, k)
     __shared__ int s_qoff[LJ_SEG_MAX_CELLS + 1];     // first quad of each cell
     __shared__ uint16_t s_flat[(LJ_LIST_THREADS / 32) * LJ_FLAT_MAX];   // per-warp candidate list
-    __shared__ int s_koff[(LJ_LIST_THREADS / 32) * 32];                  // per-warp tile offsets
+    __shared__ uint32_t s_kent[(LJ_LIST_THREADS / 32) * 32];             // per-warp entry bases
     __shared__ Tile s_t;
     __shared__ __align__(8) unsigned long long s_bar;
     if (threadIdx.x == 0) mbar_init(&s_bar, 1);
@@ -368,7 +368,7 @@ __global__ void __launch_bounds__(LJ_LIST_THREADS, 3) k_nlist(BoxDev b)
         const int nquad = s_qoff[sg.w];
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
         uint16_t* flat = s_flat + warp * LJ_FLAT_MAX;
-        int* koff = s_koff + warp * 32;
+        uint32_t* kent = s_kent + warp * 32;
         for (int qd = warp; qd < nquad; qd += LJ_LIST_THREADS / 32) {
             int cl = 0;
             while (s_qoff[cl + 1] <= qd) ++cl;                  // warp-uniform
@@ -405,10 +405,15 @@ __global__ void __launch_bounds__(LJ_LIST_THREADS, 3) k_nlist(BoxDev b)
                 if (lane >= o) incl += t;
             }
             const int total = __shfl_sync(0xffffffffu, incl, 31);
-            if (lane < 27) koff[lane] = rk.z;   // tile offset of cell k
+            // entry of tile index t from cell k: t + kent[k] (the shift digits
+            // above the slot, the slot being t minus the cell's tile offset)
+            if (lane < 27) kent[lane] = entry_make(lane, 0) - (uint32_t)rk.z;
+            const int self13 = p0q + __shfl_sync(0xffffffffu, rk.z, 13);   // tile index of the quad's first particle
             const int off = incl - len;
             int cnt[4] = {0, 0, 0, 0};
+            bool nearb[4] = {false, false, false, false};   // saw a pair within the FP64 recheck band
             const unsigned lt_mask = (1u << lane) - 1u;
+            uint32_t* const row0 = b.nbr + (size_t)b.K * p0q;   // list of the quad's first particle
             for (int w0 = 0; w0 < total; w0 += LJ_FLAT_MAX) {
                 const int wn = min(total - w0, LJ_FLAT_MAX);
                 __syncwarp();
@@ -421,37 +426,66 @@ __global__ void __launch_bounds__(LJ_LIST_THREADS, 3) k_nlist(BoxDev b)
                         flat[ok + t] = (uint16_t)((k << LJ_TILE_BITS) | (ik + t));
                 }
                 __syncwarp();
-                // one candidate per lane, tested against the quad's particles
+                // one candidate per lane, tested against the quad's particles;
+                // pairs within the recheck band are kept here and settled in
+                // FP64 afterwards
                 for (int t0 = 0; t0 < wn; t0 += 32) {
                     const int t = t0 + lane;
-                    const bool valid = t < wn;
-                    const unsigned e = valid ? flat[t] : 0u;
+                    const unsigned e = t < wn ? flat[t] : 0u;
                     const int k = (int)(e >> LJ_TILE_BITS);
                     const int idx = (int)(e & LJ_TILE_MASK);
                     const float4 pj = s_tile[idx];
                     const float4 sh = s_shift[k];
-                    const float qx = pj.x + sh.x, qy = pj.y + sh.y, qz = pj.z + sh.z;
-                    const int j = idx - koff[k];
-                    const uint32_t ent = entry_make(k, j);
+                    // lanes past the window take a far point, whose r2 is inf
+                    const float qx = t < wn ? pj.x + sh.x : 1.0e38f;
+                    const float qy = pj.y + sh.y, qz = pj.z + sh.z;
+                    const uint32_t ent = (uint32_t)idx + kent[k];
 #pragma unroll
                     for (int g = 0; g < 4; ++g) {
                         if (g >= nq) break;                           // warp-uniform
                         const float ddx = pq[g].x - qx, ddy = pq[g].y - qy, ddz = pq[g].z - qz;
                         const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                        const bool cand = valid && !(j == p0q + g && k == 13);
-                        bool in = cand && r2 < lo2;
-                        const bool band = cand && !in && r2 < hi2;
-                        if (__any_sync(0xffffffffu, band)) {          // rare: FP64 recheck near rl
-                            if (band) in = exact_within(b, R, p0q + g, j);
-                        }
+                        // tile slices are disjoint, so the index alone finds the particle itself
+                        const bool in = r2 < hi2 && idx != self13 + g;
+                        nearb[g] = nearb[g] || (in && r2 >= lo2);
                         const unsigned bits = __ballot_sync(0xffffffffu, in);
-                        if (in) {
-                            const int pos = cnt[g] + __popc(bits & lt_mask);
-                            if (pos < b.K) b.nbr[(size_t)b.K * (p0q + g) + pos] = ent;
-                        }
+                        const int pos = cnt[g] + __popc(bits & lt_mask);
+                        if (in && pos < b.K) row0[(size_t)b.K * g + pos] = ent;
                         cnt[g] += __popc(bits);
                     }
                 }
+            }
+            // FP64 decision for the particles that saw a pair near rl: drop the
+            // band pairs beyond rl and compact their lists
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+                if (g >= nq || !__any_sync(0xffffffffu, nearb[g])) continue;   // warp-uniform
+                __syncwarp();   // the list's entries, stored by other lanes, are visible
+                const int p = p0q + g;
+                uint32_t* const row = row0 + (size_t)b.K * g;
+                const int c = min(cnt[g], b.K);
+                int kept = 0;
+                for (int s0 = 0; s0 < c; s0 += 32) {
+                    const int s = s0 + lane;
+                    bool keep = false;
+                    uint32_t ent = 0;
+                    if (s < c) {
+                        ent = row[s];
+                        const int j = (int)(ent & LJ_IDX_MASK);
+                        const int k = entry_k(ent);
+                        const float4 pj = b.posq[j];
+                        const float4 sh = s_shift[k];
+                        const float ddx = pq[g].x - (pj.x + sh.x), ddy = pq[g].y - (pj.y + sh.y),
+                                    ddz = pq[g].z - (pj.z + sh.z);
+                        const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                        keep = r2 < lo2 || exact_within(b, R, p, j);
+                    }
+                    const unsigned bits = __ballot_sync(0xffffffffu, keep);
+                    __syncwarp();
+                    if (keep) row[kept + __popc(bits & lt_mask)] = ent;
+                    kept += __popc(bits);
+                }
+                cnt[g] = cnt[g] - c + kept;   // entries beyond the capacity are counted, not stored
             }
             if (lane < nq) {
                 const int c = lane == 0 ? cnt[0] : lane == 1 ? cnt[1] : lane == 2 ? cnt[2] : cnt[3];
