@@ -11,9 +11,10 @@
 //
 // Sequence: k_bin (new cell of every particle, counts) -> k_scan_tiles +
 // k_scan_add (exclusive scan of the counts per replica) -> k_scatter (slot
-// per particle) -> k_sortgather (order inside each cell by user index, so
-// the layout is a deterministic function of the positions; gather into the
-// sorted arrays) -> k_nlist (27-cell search).
+// per particle) -> k_sortgather (order inside each cell by FP32 z offset,
+// ties by user index, so the layout is a deterministic function of the
+// positions; gather into the sorted arrays) -> k_nlist (27-cell search,
+// each neighbour cell narrowed to its candidates within reach along z).
 #include <climits>
 
 #include "ljmd_internal.cuh"
@@ -210,10 +211,22 @@ __global__ void __launch_bounds__(LJ_CHUNK) k_scatter(BoxDev b)
 }
 
 // ---------------------------------------------------------------------------
-// k_sortgather: one warp per cell.  Rank every member of the cell by user
-// index (count of smaller keys; keys are unique), then gather its state into
-// the sorted arrays and derive its cell-relative offset and FP32 copy.
+// k_sortgather: one warp per cell.  Order the members of the cell by their
+// FP32 z offset from the cell centre (the value posq will hold), ties by
+// user index (count of smaller keys; keys are unique), so the layout is a
+// deterministic function of the positions and the list build can take, in
+// every neighbour cell, the contiguous run of candidates within reach along
+// z.  Gather the state into the sorted arrays and derive the cell-relative
+// offsets and their FP32 copy.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long sort_key(const BoxDev& b, int p, double zc)
+{
+    const float z = __double2float_rn(b.xabsB[2 * b.np + p] - zc);
+    const unsigned u = __float_as_uint(z);
+    const unsigned ord = (u & 0x80000000u) ? ~u : (u | 0x80000000u);   // order-preserving
+    return ((unsigned long long)ord << 32) | (unsigned)b.uidB[p];
+}
+
 __global__ void __launch_bounds__(256) k_sortgather(BoxDev b)
 {
     if (!box_needs_rebuild(b)) return;
@@ -232,13 +245,15 @@ __global__ void __launch_bounds__(256) k_sortgather(BoxDev b)
         for (int base = 0; base < n; base += 32) {
             int idx = base + lane;
             int p = idx < n ? b.perm[s0 + idx] : -1;
-            int key = idx < n ? b.uidB[p] : INT_MAX;
+            const unsigned long long none = ~0ull;
+            unsigned long long key = idx < n ? sort_key(b, p, centre[2]) : none;
             int rank = 0;
             for (int b2 = 0; b2 < n; b2 += 32) {
-                int k2 = (b2 + lane < n) ? b.uidB[b.perm[s0 + b2 + lane]] : INT_MAX;
+                unsigned long long k2 =
+                    b2 == base ? key : ((b2 + lane < n) ? sort_key(b, b.perm[s0 + b2 + lane], centre[2]) : none);
 #pragma unroll 8
                 for (int t = 0; t < 32; ++t) {
-                    int kt = __shfl_sync(0xffffffffu, k2, t);
+                    unsigned long long kt = __shfl_sync(0xffffffffu, k2, t);
                     rank += (kt < key) ? 1 : 0;
                 }
             }
@@ -264,7 +279,7 @@ __global__ void __launch_bounds__(256) k_sortgather(BoxDev b)
                     copy_acc(b, b.vel, b.velB, c, q, p);
                     b.img[c * b.np + q] = b.imgB[c * b.np + p];
                 }
-                b.uid[q] = key;
+                b.uid[q] = b.uidB[p];
                 b.type[q] = ty;
                 b.cell[q] = gc;
                 float4 pq = make_float4(of[0], of[1], of[2], __int_as_float(ty));
@@ -354,6 +369,10 @@ __global__ void __launch_bounds__(LJ_LIST_THREADS, 3) k_nlist(BoxDev b)
         if (s_t.total > 0 && !stage_tile_bulk(b.posq, s_t, s_tile, &s_bar, phase, b.err)) return;
         const float ell_h[3] = {0.5f * R.ellf[0], 0.5f * R.ellf[1], 0.5f * R.ellf[2]};
         const float rcull = b.rl2f + b.band;
+        // reach along z of any pair the FP32 test can accept (r2 < rl^2 +
+        // band implies dz^2 < rl^2 + band), with a margin for the rounding of
+        // the shifted z values
+        const float zreach = sqrtf(rcull) + 1e-3f;
         // work units: quads of particles of one cell (the 4 groups of a warp
         // share the cell, so their candidate loops are identical)
         if (threadIdx.x == 0) {
@@ -389,14 +408,39 @@ __global__ void __launch_bounds__(LJ_LIST_THREADS, 3) k_nlist(BoxDev b)
                 rk = rng[lane];
                 const float4 sh = s_shift[lane];
                 bool far = true;
+                float zmin = pq[0].z, zmax = pq[0].z;
 #pragma unroll
                 for (int g = 0; g < 4; ++g) {
                     const float gx = fmaxf(fabsf(pq[g].x - sh.x) - ell_h[0], 0.f);
                     const float gy = fmaxf(fabsf(pq[g].y - sh.y) - ell_h[1], 0.f);
                     const float gz = fmaxf(fabsf(pq[g].z - sh.z) - ell_h[2], 0.f);
                     far = far && (g >= nq || gx * gx + gy * gy + gz * gz >= rcull);
+                    zmin = fminf(zmin, pq[g].z);   // g >= nq repeats particle 0
+                    zmax = fmaxf(zmax, pq[g].z);
                 }
-                len = far ? 0 : rk.y - rk.x;
+                if (!far) {
+                    // the cell is sorted by z offset: keep the run with
+                    // z_j + shift_z within zreach of the quad's z range
+                    const float zlo = zmin - zreach - sh.z, zhi = zmax + zreach - sh.z;
+                    const float* tz = reinterpret_cast<const float*>(s_tile) + 2;   // .z of tile entry t: tz[4 t]
+                    int lo = rk.x + rk.z, hi = rk.y + rk.z;
+                    while (lo < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        if (tz[4 * mid] < zlo) lo = mid + 1;
+                        else hi = mid;
+                    }
+                    int e = rk.y + rk.z;
+                    hi = e;
+                    int lo2 = lo;
+                    while (lo2 < hi) {
+                        const int mid = (lo2 + hi) >> 1;
+                        if (tz[4 * mid] <= zhi) lo2 = mid + 1;
+                        else hi = mid;
+                    }
+                    rk.x = lo - rk.z;
+                    rk.y = lo2 - rk.z;
+                    len = rk.y - rk.x;
+                }
             }
             int incl = len;
 #pragma unroll

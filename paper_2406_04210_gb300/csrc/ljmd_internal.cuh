@@ -2,8 +2,8 @@
 //
 // Layout in HBM (one batch of nrep replicas, np particle slots):
 //   * particles of replica r occupy slots [p_off, p_off + n) with p_off a
-//     multiple of 32; slots are sorted by (cell, user index) at every list
-//     build (particle binning, Sec. 3 "Code structure").
+//     multiple of 32; slots are sorted by (cell, FP32 z offset, user index)
+//     at every list build (particle binning, Sec. 3 "Code structure").
 //   * the integrator state of a particle is its cell id plus the offset from
 //     that cell's centre ("cell-relative offset"), so FP32 copies of the
 //     offsets keep ~1e-7 absolute resolution whatever the box size.  In
