@@ -276,22 +276,17 @@ __global__ void __launch_bounds__(LJ_F64_THREADS) k_force_f64(BoxDev b)
     }
 }
 
-// One block per replica: E_pot, E_kin, W, T from the per-chunk partial sums,
-// summed in a fixed order (deterministic): thread t takes chunks t, t+B, ...
-__global__ void __launch_bounds__(512) k_thermo(BoxDev b, double* out, int with_kin)
+// E_pot, E_kin, W, T per replica from the per-chunk partial sums, in a
+// fixed order (deterministic): each block sums one item (a run of up to 256
+// chunks of one replica) and stores its 3 sums; the block that completes a
+// replica's last item (atomic count) adds the replica's item sums in item
+// order and resets the count.
+__global__ void __launch_bounds__(256) k_thermo(BoxDev b, double* out, int with_kin)
 {
-    __shared__ double s_red[3][512 / 32];
+    __shared__ double s_red[3][256 / 32];
+    __shared__ int s_last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int r = blockIdx.x; r < b.nrep; r += gridDim.x) {
-        const RepDev& R = b.rep[r];
-        double e = 0.0, w = 0.0, k = 0.0;
-        for (int c = R.chunk_off + (int)threadIdx.x; c < R.chunk_off + R.nchunk; c += blockDim.x) {
-            e += b.part_f[2 * c];
-            w += b.part_f[2 * c + 1];
-        }
-        if (with_kin)
-            for (int c = R.chunk_off + (int)threadIdx.x; c < R.chunk_off + R.nchunk; c += blockDim.x)
-                k += b.part_k[c];
+    auto block_sum3 = [&](double& e, double& w, double& k) {
         e = warp_sum_d(e);
         w = warp_sum_d(w);
         k = warp_sum_d(k);
@@ -308,10 +303,44 @@ __global__ void __launch_bounds__(512) k_thermo(BoxDev b, double* out, int with_
                 w += s_red[1][q];
                 k += s_red[2][q];
             }
-            out[4 * r + 0] = e;
-            out[4 * r + 1] = k;
-            out[4 * r + 2] = w;
-            out[4 * r + 3] = R.n > 1 ? 2.0 * k / (3.0 * (double)R.n - 3.0) : 0.0;
+        }
+        __syncthreads();
+    };
+    for (int it = blockIdx.x; it < b.ntitem; it += gridDim.x) {
+        const int4 t = b.titem[it];
+        const int r = t.x;
+        const RepDev& R = b.rep[r];
+        double e = 0.0, w = 0.0, k = 0.0;
+        for (int c = t.y + (int)threadIdx.x; c < t.z; c += blockDim.x) {
+            e += b.part_f[2 * c];
+            w += b.part_f[2 * c + 1];
+            if (with_kin) k += b.part_k[c];
+        }
+        block_sum3(e, w, k);
+        if (threadIdx.x == 0) {
+            b.part_t[3 * it + 0] = e;
+            b.part_t[3 * it + 1] = w;
+            b.part_t[3 * it + 2] = k;
+            __threadfence();
+            s_last = atomicAdd(&b.tcount[r], 1u) == (unsigned)(R.nti - 1);
+        }
+        __syncthreads();
+        if (s_last) {   // block-uniform
+            __threadfence();
+            e = w = k = 0.0;
+            for (int i = R.ti_off + (int)threadIdx.x; i < R.ti_off + R.nti; i += blockDim.x) {
+                e += __ldcg(&b.part_t[3 * i + 0]);
+                w += __ldcg(&b.part_t[3 * i + 1]);
+                k += __ldcg(&b.part_t[3 * i + 2]);
+            }
+            block_sum3(e, w, k);
+            if (threadIdx.x == 0) {
+                out[4 * r + 0] = e;
+                out[4 * r + 1] = k;
+                out[4 * r + 2] = w;
+                out[4 * r + 3] = R.n > 1 ? 2.0 * k / (3.0 * (double)R.n - 3.0) : 0.0;
+                b.tcount[r] = 0u;
+            }
         }
         __syncthreads();
     }
@@ -336,6 +365,6 @@ cudaError_t launch_force(const BoxDev& b, int energy, Launch l)
 
 cudaError_t launch_thermo(const BoxDev& b, double* out, int with_kin, Launch l)
 {
-    k_thermo<<<l.grid, 512, 0, l.s>>>(b, out, with_kin);
+    k_thermo<<<l.grid, 256, 0, l.s>>>(b, out, with_kin);
     return cudaGetLastError();
 }

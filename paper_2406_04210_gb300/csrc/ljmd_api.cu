@@ -68,6 +68,7 @@ struct md_box {
     int np = 0;
     std::vector<RepDev> reps;
     std::vector<int4> chunks;
+    std::vector<int4> titems;   // energy-reduction items
     std::vector<int4> tiles;
     std::vector<int4> segs;
     // LJ
@@ -230,6 +231,7 @@ void invalidate_graphs(md_box* b)
 }
 
 Launch lch(md_box* b) { return Launch{std::max(1, std::min((int)b->d.nchunk, b->nsm * 12)), LJ_CHUNK, b->stream}; }
+Launch lthermo(md_box* b) { return Launch{std::max(1, std::min(b->d.ntitem, b->nsm * 8)), 256, b->stream}; }
 Launch lcell(md_box* b) { return Launch{std::max(1, std::min((b->d.ncell + 7) / 8, b->nsm * 8)), 256, b->stream}; }
 Launch lseg(md_box* b) { return Launch{std::max(1, std::min(b->d.nseg, b->nsm * 8)), LJ_SEG_THREADS, b->stream}; }
 Launch lforce(md_box* b)
@@ -313,8 +315,7 @@ md_status enqueue_force(md_box* b, int energy, double* thermo_out_dev)
     CK(b, launch_force(b->d, energy, lforce(b)));
     b->launches += 1;
     if (energy && thermo_out_dev) {
-        Launch lt{std::max(1, std::min(b->nrep, b->nsm * 4)), 512, b->stream};
-        CK(b, launch_thermo(b->d, thermo_out_dev, 0, lt));
+        CK(b, launch_thermo(b->d, thermo_out_dev, 0, lthermo(b)));
         b->launches += 1;
     }
     return MD_OK;
@@ -494,7 +495,7 @@ md_status enqueue_steps(md_box* b, int64_t n, double dt, int energy, double* rin
                         bool tape = false)
 {
     Launch l = lch(b);
-    Launch lt{std::max(1, std::min(b->nrep, b->nsm * 4)), 512, b->stream};
+    Launch lt = lthermo(b);
     size_t rs = (size_t)b->nrep * 4;
     auto mark = [&](int64_t s, int ph, int end) -> cudaError_t {
         if (!ge) return cudaSuccess;
@@ -733,6 +734,10 @@ md_status md_batch_create(md_box** out, int32_t nrep, const int64_t* n, const do
             b->chunks.push_back(make_int4(r, (int)(poff + p), (int)(poff + std::min<int64_t>(p + LJ_CHUNK, n[r])),
                                           (int)b->chunks.size()));
         R.nchunk = (int)b->chunks.size() - R.chunk_off;
+        R.ti_off = (int)b->titems.size();
+        for (int c = 0; c < std::max(1, R.nchunk); c += 256)
+            b->titems.push_back(make_int4(r, R.chunk_off + c, R.chunk_off + std::min(c + 256, R.nchunk), 0));
+        R.nti = (int)b->titems.size() - R.ti_off;
         b->reps.push_back(R);
         poff += round_up(n[r], 32);
         uoff += n[r];
@@ -743,6 +748,14 @@ md_status md_batch_create(md_box** out, int32_t nrep, const int64_t* n, const do
         size_t np3 = 3 * (size_t)b->np;
         CKS(dev_alloc(b, &b->d_rep, b->reps.size()));
         CKS(dev_alloc(b, &b->d_chunk, b->chunks.size()));
+        int4* ti;
+        CKS(dev_alloc(b, &ti, b->titems.size(), false));
+        CK(b, cudaMemcpyAsync(ti, b->titems.data(), sizeof(int4) * b->titems.size(), cudaMemcpyHostToDevice,
+                              b->stream));
+        d.titem = ti;
+        d.ntitem = (int)b->titems.size();
+        CKS(dev_alloc(b, &d.part_t, 3 * b->titems.size()));
+        CKS(dev_alloc(b, &d.tcount, nrep));
         CKS(dev_alloc(b, &b->d_lj, 1));
         CK(b, cudaMemcpyAsync(b->d_chunk, b->chunks.data(), sizeof(int4) * b->chunks.size(),
                               cudaMemcpyHostToDevice, b->stream));
@@ -1536,8 +1549,7 @@ extern "C" md_status md_force_noalloc(md_box* b, double* force_out, double* epot
     double* th = scratch + 2 * nchunk;        // nrep x (E_pot, E_kin, W, T), overwritten
     CKS(clear_err(b));
     CK(b, launch_force(v, 1, lforce(b)));
-    Launch lt{std::max(1, std::min(b->nrep, b->nsm * 4)), 512, b->stream};
-    CK(b, launch_thermo(v, th, 0, lt));
+    CK(b, launch_thermo(v, th, 0, lthermo(b)));
     if (force_out && b->ntot > 0) CK(b, launch_force_out(b->d, force_out, lch(b)));
     if (epot)
         CK(b, cudaMemcpy2DAsync(epot, sizeof(double), th + 0, 4 * sizeof(double), sizeof(double), b->nrep,

@@ -70,6 +70,7 @@ struct RepDev {
     int p_off, n;              // first slot, real particles
     int u_off;                 // first user index
     int chunk_off, nchunk;     // particle work items of this replica
+    int ti_off, nti;           // energy-reduction items of this replica
     int seg_off, nseg;         // segments of this replica
     int S;                     // cells per segment (along x)
 };
@@ -113,6 +114,8 @@ struct BoxDev {
     double rl2;
     const RepDev* rep;
     const int4* chunk;         // (rep, p_begin, p_end, chunk index)
+    const int4* titem;         // energy reduction: (rep, first chunk, end chunk, 0)
+    int ntitem;
     const int4* seg;           // (rep, first cell x, row = cy + ny cz, cells)
     int nseg;
     const LJDev* lj;
@@ -153,6 +156,8 @@ struct BoxDev {
     // per-chunk FP64 partial sums
     double* part_f;            // [chunk*2 + 0] = E_pot share, [+1] = W share
     double* part_k;            // [chunk] = E_kin share
+    double* part_t;            // [item*3 + 0..2] = E_pot, W, E_kin of a reduction item
+    unsigned* tcount;          // per replica: reduction items finished (last one resets)
 };
 
 // ---- double-single helpers (Dekker / Knuth error-free transformations) ----
