@@ -86,9 +86,16 @@ __device__ __forceinline__ void pair_f32(unsigned ent, const float4& pj, bool va
 
 // FP32 pair force (Sec. 4/5), one 128-particle chunk per block pass, LJ_TPP
 // threads per particle.  The 8 threads of a particle take entries s, s+8,
-// ... of its list (two at a time for instruction-level parallelism), gather
-// the neighbours' FP32 offsets through L1 and combine their partial forces
-// with shuffles.  MONO: a single species, parameters in registers.
+// ... of its list in blocks of GB entries per thread (the block's GB
+// gathers in flight at once, the next block's entries already loading, two
+// independent pair chains at a time), gather the neighbours' FP32 offsets
+// through L1 and combine their partial forces with shuffles.  Slots past
+// the list's end gather the particle itself and are masked.  GB = 2 (16
+// entries of the particle per block) keeps that padding small for lists of
+// ~80 entries; deeper blocks (4, 8) measured slower on the 4M-particle fluid
+// although they keep more loads in flight.  MONO: a single species,
+// parameters in registers.
+constexpr int GB = 2;   // row entries per thread per block
 template <bool MONO, bool ENERGY>
 __global__ void __launch_bounds__(LJ_FORCE_THREADS, 4) k_force_f32(BoxDev b)
 {
@@ -142,34 +149,34 @@ __global__ void __launch_bounds__(LJ_FORCE_THREADS, 4) k_force_f32(BoxDev b)
             // of the particle) is loaded at once and the next block is in
             // flight while this one is computed
             const unsigned self = entry_make(13, act ? p : 0);
-            unsigned cur[8], nxt[8];
+            unsigned cur[GB], nxt[GB];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
+            for (int i = 0; i < GB; ++i) {
                 const int s = l8 + LJ_TPP * i;
                 cur[i] = s < cnt ? __ldcs(L + s) : self;
             }
             float fx = 0.f, fy = 0.f, fz = 0.f, fx2 = 0.f, fy2 = 0.f, fz2 = 0.f;
-            for (int blk = 0; blk * 8 * LJ_TPP < cnt; ++blk) {
-                const int nb = (blk + 1) * 8 * LJ_TPP;
+            for (int blk = 0; blk * GB * LJ_TPP < cnt; ++blk) {
+                const int nb = (blk + 1) * GB * LJ_TPP;
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
+                for (int i = 0; i < GB; ++i) {
                     const int s = nb + l8 + LJ_TPP * i;
                     nxt[i] = s < cnt ? __ldcs(L + s) : self;
                 }
                 // the neighbours of the whole block: eight gathers in flight
-                float4 pj[8];
+                float4 pj[GB];
 #pragma unroll
-                for (int i = 0; i < 8; ++i) pj[i] = __ldg(posq + (cur[i] & LJ_IDX_MASK));
+                for (int i = 0; i < GB; ++i) pj[i] = __ldg(posq + (cur[i] & LJ_IDX_MASK));
 #pragma unroll
-                for (int i = 0; i < 8; i += 2) {
-                    const int s = blk * 8 * LJ_TPP + l8 + LJ_TPP * i;
+                for (int i = 0; i < GB; i += 2) {
+                    const int s = blk * GB * LJ_TPP + l8 + LJ_TPP * i;
                     pair_f32<MONO, ENERGY>(cur[i], pj[i], s < cnt, pi, ti, ell, s_lj, s_rc2, s_esh, nt, mlj,
                                            mrc2, mesh, fx, fy, fz, e, vir);
                     pair_f32<MONO, ENERGY>(cur[i + 1], pj[i + 1], s + LJ_TPP < cnt, pi, ti, ell, s_lj, s_rc2,
                                            s_esh, nt, mlj, mrc2, mesh, fx2, fy2, fz2, e, vir);
                 }
 #pragma unroll
-                for (int i = 0; i < 8; ++i) cur[i] = nxt[i];
+                for (int i = 0; i < GB; ++i) cur[i] = nxt[i];
             }
             fx += fx2;
             fy += fy2;
