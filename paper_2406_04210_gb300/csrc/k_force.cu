@@ -85,17 +85,17 @@ __device__ __forceinline__ void pair_f32(unsigned ent, const float4& pj, bool va
 }
 
 // FP32 pair force (Sec. 4/5), one 128-particle chunk per block pass, LJ_TPP
-// threads per particle.  The 8 threads of a particle take entries s, s+8,
-// ... of its list in blocks of GB entries per thread (the block's GB
+// (4) threads per particle.  The threads of a particle take entries s,
+// s+4, ... of its list in blocks of GB entries per thread (the block's GB
 // gathers in flight at once, the next block's entries already loading, two
 // independent pair chains at a time), gather the neighbours' FP32 offsets
 // through L1 and combine their partial forces with shuffles.  Slots past
-// the list's end gather the particle itself and are masked.  GB = 2 (16
-// entries of the particle per block) keeps that padding small for lists of
-// ~80 entries; deeper blocks (4, 8) measured slower on the 4M-particle fluid
-// although they keep more loads in flight.  MONO: a single species,
-// parameters in registers.
-constexpr int GB = 2;   // row entries per thread per block
+// the list's end gather the particle itself and are masked.  With 4 threads
+// and GB = 4 a block covers 16 entries of the particle, so lists of ~80
+// entries carry little padding; on the 4M-particle fluid this measured
+// fastest among 2/4/8 threads per particle x 2/4/8 entries per thread.
+// MONO: a single species, parameters in registers.
+constexpr int GB = 4;   // row entries per thread per block
 template <bool MONO, bool ENERGY>
 __global__ void __launch_bounds__(LJ_FORCE_THREADS, 4) k_force_f32(BoxDev b)
 {
@@ -145,9 +145,9 @@ __global__ void __launch_bounds__(LJ_FORCE_THREADS, 4) k_force_f32(BoxDev b)
             }
             const int ti = __float_as_int(pi.w);
             const uint32_t* L = b.nbr + (size_t)K * p;
-            // lane l8 takes entries l8 + 8i; a block of 8 of them (64 entries
-            // of the particle) is loaded at once and the next block is in
-            // flight while this one is computed
+            // thread l8 takes entries l8 + LJ_TPP i; a block of GB of them is
+            // loaded at once and the next block is in flight while this one
+            // is computed
             const unsigned self = entry_make(13, act ? p : 0);
             unsigned cur[GB], nxt[GB];
 #pragma unroll

@@ -21,11 +21,11 @@
 //     d_ij = (o_i - o_j) - (dx, dy, dz) * cell edge, decoded with integer and
 //     FP32 arithmetic (no table).  The stencil code k = 9(dz+1) + 3(dy+1) +
 //     (dx+1) orders the 27 cells.
-//     Entry s of particle p is nbr[p K + s] (K a multiple of 8): the 8 threads
-//     of a particle read 8 consecutive entries (one 32-byte sector) at a time.
+//     Entry s of particle p is nbr[p K + s] (K a multiple of 8): the 4 threads
+//     of a particle read 4 consecutive entries at a time.
 //   * the list build works per segment with the tile staged in shared memory;
-//     the pair-force kernels work per 128-particle chunk, 8 threads per
-//     particle, and gather neighbour offsets through L1 (the 32 particles of a
+//     the pair-force kernels work per 128-particle chunk, 4 threads per
+//     particle, and gather neighbour offsets through L1 (the 64 particles of a
 //     block pass are consecutive, so they share one 27-cell neighbourhood).
 #pragma once
 
@@ -43,7 +43,7 @@
 #define LJ_FORCE_THREADS 256   // threads of the FP32 pair-force kernel
 #define LJ_LIST_THREADS 256    // threads of the list-build kernel
 #define LJ_F64_THREADS 128     // threads of the FP64 pair kernel (one per particle)
-#define LJ_TPP 8               // threads per particle in the pair kernels
+#define LJ_TPP 4               // threads per particle in the pair kernels
 #define LJ_SEG_MAX_CELLS 16    // most cells in one segment
 #define LJ_FLAT_MAX 1024       // candidates of one cell's 27-cell neighbourhood (list build)
 #define LJ_LIST_SMEM (32 * 1024)   // bytes of a segment's list staged in smem
