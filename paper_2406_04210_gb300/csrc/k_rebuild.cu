@@ -324,11 +324,15 @@ __global__ void __launch_bounds__(LJ_LIST_THREADS, 3) k_nlist(BoxDev b)
     __shared__ uint32_t s_kent[(LJ_LIST_THREADS / 32) * 32];             // per-warp entry bases
     __shared__ Tile s_t;
     __shared__ __align__(8) unsigned long long s_bar;
-    if (threadIdx.x == 0) mbar_init(&s_bar, 1);
+    __shared__ int s_next;      // next quad of the segment to hand out
+    __shared__ int s_longest;   // longest list this block built
+    if (threadIdx.x == 0) {
+        mbar_init(&s_bar, 1);
+        s_longest = 0;
+    }
     unsigned phase = 0;
     int cur_r = -1;
     const float lo2 = b.rl2f - b.band, hi2 = b.rl2f + b.band;
-    // LJ_TPP threads per particle: lanes l8 of group grp share the particle
     for (int w = blockIdx.x; w < b.nseg; w += gridDim.x) {
         int4 sg = b.seg[w];
         int r = sg.x;
@@ -373,8 +377,9 @@ __global__ void __launch_bounds__(LJ_LIST_THREADS, 3) k_nlist(BoxDev b)
         // band implies dz^2 < rl^2 + band), with a margin for the rounding of
         // the shifted z values
         const float zreach = sqrtf(rcull) + 1e-3f;
-        // work units: quads of particles of one cell (the 4 groups of a warp
-        // share the cell, so their candidate loops are identical)
+        // work units: quads of particles of one cell (the quad's particles
+        // share the cell, so their candidates are the same), handed out to
+        // the warps one at a time as they finish
         if (threadIdx.x == 0) {
             int q = 0;
             for (int cl = 0; cl < sg.w; ++cl) {
@@ -382,13 +387,14 @@ __global__ void __launch_bounds__(LJ_LIST_THREADS, 3) k_nlist(BoxDev b)
                 q += (b.cell_end[c0 + cl] - b.cell_start[c0 + cl] + 3) >> 2;
             }
             s_qoff[sg.w] = q;
+            s_next = LJ_LIST_THREADS / 32;
         }
         __syncthreads();
         const int nquad = s_qoff[sg.w];
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
         uint16_t* flat = s_flat + warp * LJ_FLAT_MAX;
         uint32_t* kent = s_kent + warp * 32;
-        for (int qd = warp; qd < nquad; qd += LJ_LIST_THREADS / 32) {
+        for (int qd = warp; qd < nquad;) {
             int cl = 0;
             while (s_qoff[cl + 1] <= qd) ++cl;                  // warp-uniform
             const int cs = b.cell_start[c0 + cl], ce = b.cell_end[c0 + cl];
@@ -486,11 +492,11 @@ __global__ void __launch_bounds__(LJ_LIST_THREADS, 3) k_nlist(BoxDev b)
                     const uint32_t ent = (uint32_t)idx + kent[k];
 #pragma unroll
                     for (int g = 0; g < 4; ++g) {
-                        if (g >= nq) break;                           // warp-uniform
                         const float ddx = pq[g].x - qx, ddy = pq[g].y - qy, ddz = pq[g].z - qz;
                         const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                        // tile slices are disjoint, so the index alone finds the particle itself
-                        const bool in = r2 < hi2 && idx != self13 + g;
+                        // tile slices are disjoint, so the index alone finds the
+                        // particle itself; slots past the quad's end take nothing
+                        const bool in = r2 < hi2 && idx != self13 + g && g < nq;
                         nearb[g] = nearb[g] || (in && r2 >= lo2);
                         const unsigned bits = __ballot_sync(0xffffffffu, in);
                         const int pos = cnt[g] + __popc(bits & lt_mask);
@@ -531,18 +537,25 @@ __global__ void __launch_bounds__(LJ_LIST_THREADS, 3) k_nlist(BoxDev b)
                 }
                 cnt[g] = cnt[g] - c + kept;   // entries beyond the capacity are counted, not stored
             }
+            const int c = lane == 0 ? cnt[0] : lane == 1 ? cnt[1] : lane == 2 ? cnt[2] : cnt[3];
             if (lane < nq) {
-                const int c = lane == 0 ? cnt[0] : lane == 1 ? cnt[1] : lane == 2 ? cnt[2] : cnt[3];
-                const int p = p0q + lane;
-                b.nbr_count[p] = c;
-                atomicMax(&b.err[2], c);   // longest list of this build
+                b.nbr_count[p0q + lane] = c;
                 if (c > b.K) {
                     atomicOr(&b.err[0], LJ_ERRBIT_CAPACITY);
                     atomicMax(&b.err[1], c);
                 }
             }
+            const int cmax = __reduce_max_sync(0xffffffffu, lane < nq ? c : 0);
+            int nxt = 0;
+            if (lane == 0) {
+                atomicMax(&s_longest, cmax);
+                nxt = atomicAdd(&s_next, 1);
+            }
+            qd = __shfl_sync(0xffffffffu, nxt, 0);
         }
     }
+    __syncthreads();
+    if (threadIdx.x == 0 && s_longest > 0) atomicMax(&b.err[2], s_longest);   // longest list of this build
 }
 
 }  // namespace
