@@ -1163,34 +1163,77 @@ md_status md_adjoint(md_box* b, const double* lam_x_T, const double* lam_v_T, do
     Launch lf = lforce(b);
     const int nchunk = (int)b->chunks.size();
     const int twoP = 2 * P;
+    // The replay of a segment (k recorded steps keeping the tape) and its
+    // reverse sweep have the same launches for every segment: each is
+    // captured once into a CUDA graph and launched per segment.  The reverse
+    // sweep has four forms: the last segment also starts from the final
+    // state's HVP, and the first weights its last term by h/2.
+    struct Graphs {
+        cudaGraphExec_t g[5] = {};
+        int64_t kernels[5] = {};
+        ~Graphs()
+        {
+            for (auto e : g)
+                if (e) cudaGraphExecDestroy(e);
+        }
+    } graphs;
+    auto capture = [&](int slot, auto&& fn) -> md_status {
+        const int64_t l0 = b->launches;
+        CK(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        md_status st = fn();
+        cudaGraph_t graph = nullptr;
+        cudaError_t ce = cudaStreamEndCapture(b->stream, &graph);
+        graphs.kernels[slot] = b->launches - l0;
+        b->launches = l0;
+        if (st != MD_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (ce != cudaSuccess) return cuda_fail(b, ce, "cudaStreamEndCapture");
+        ce = cudaGraphInstantiate(&graphs.g[slot], graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) return cuda_fail(b, ce, "cudaGraphInstantiate");
+        return MD_OK;
+    };
+    auto launch = [&](int slot) -> md_status {
+        CK(b, cudaGraphLaunch(graphs.g[slot], b->stream));
+        b->launches += graphs.kernels[slot];
+        return MD_OK;
+    };
+    auto reverse = [&](bool last, bool first) -> md_status {
+        for (int m = k; m >= 0; --m) {
+            BoxDev v = tape_view(b, m);
+            if (m == k) {
+                if (!last) continue;   // this state's HVP was done at m = 0 of the next segment
+                CK(b, launch_adj_pre(v, b->d_lx, b->d_lv, b->d_g, b->d_u, h, 0, l));
+                CK(b, launch_hvp(v, b->d_u, b->d_hu, b->d_partg, lf));
+                CK(b, launch_adj_post(v, b->d_lx, b->d_g, b->d_hu, h, 0, l));
+                CK(b, launch_param_reduce(b->d_partg, nchunk, twoP, b->d_wts, b->d_theta, b->stream));
+            } else {
+                CK(b, launch_adj_pre(v, b->d_lx, b->d_lv, b->d_g, b->d_u, h, 1, l));
+                CK(b, launch_hvp(v, b->d_u, b->d_hu, b->d_partg, lf));
+                CK(b, launch_adj_post(v, b->d_lx, b->d_g, b->d_hu, h, 1, l));
+                CK(b, launch_param_reduce(b->d_partg, nchunk, twoP, b->d_wts + ((first && m == 0) ? 0 : 1),
+                                          b->d_theta, b->stream));
+            }
+            b->launches += 4;
+        }
+        return MD_OK;
+    };
     for (int c = C - 1; c >= 0; --c) {
         // replay segment c, keeping every state's HVP inputs on the tape
         CKS(ckpt_copy(b, c, true));
         CKS(clear_err(b));
         CKS(replay_lists(b));
         CKS(tape_save(b, 0));
-        CKS(enqueue_steps(b, k, h, 0, nullptr, nullptr, true));
+        if (!graphs.g[4]) CKS(capture(4, [&]() { return enqueue_steps(b, k, h, 0, nullptr, nullptr, true); }));
+        CKS(launch(4));
         int e2[3];
         CKS(read_err(b, e2));
         if (e2[0]) return fail(b, MD_ERR_CAPACITY, "md_adjoint: replay of a segment failed");
-        for (int m = k; m >= 0; --m) {
-            BoxDev v = tape_view(b, m);
-            if (m == k) {
-                if (c != C - 1) continue;   // this state's HVP was done at m = 0 of segment c + 1
-                CK(b, launch_adj_pre(v, b->d_lx, b->d_lv, b->d_g, b->d_u, h, 0, l));
-                CK(b, launch_hvp(v, b->d_u, b->d_hu, b->d_partg, lf));
-                CK(b, launch_adj_post(v, b->d_lx, b->d_g, b->d_hu, h, 0, l));
-                CK(b, launch_param_reduce(b->d_partg, nchunk, twoP, b->d_wts, b->d_theta, b->stream));
-            } else {
-                const bool first = (c == 0 && m == 0);
-                CK(b, launch_adj_pre(v, b->d_lx, b->d_lv, b->d_g, b->d_u, h, 1, l));
-                CK(b, launch_hvp(v, b->d_u, b->d_hu, b->d_partg, lf));
-                CK(b, launch_adj_post(v, b->d_lx, b->d_g, b->d_hu, h, 1, l));
-                CK(b, launch_param_reduce(b->d_partg, nchunk, twoP, b->d_wts + (first ? 0 : 1), b->d_theta,
-                                          b->stream));
-            }
-            b->launches += 4;
-        }
+        const int form = (c == C - 1 ? 1 : 0) | (c == 0 ? 2 : 0);
+        if (!graphs.g[form]) CKS(capture(form, [&]() { return reverse(c == C - 1, c == 0); }));
+        CKS(launch(form));
     }
     // outputs
     bool dx = is_device_ptr(lam_x_0), dv = is_device_ptr(lam_v_0);
