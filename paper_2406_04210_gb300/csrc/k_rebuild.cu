@@ -467,13 +467,12 @@ __global__ void __launch_bounds__(LJ_LIST_THREADS, 3) k_nlist(BoxDev b)
             for (int w0 = 0; w0 < total; w0 += LJ_FLAT_MAX) {
                 const int wn = min(total - w0, LJ_FLAT_MAX);
                 __syncwarp();
-                for (int k = 0; k < 27; ++k) {
-                    const int lk = __shfl_sync(0xffffffffu, len, k);
-                    const int ok = __shfl_sync(0xffffffffu, off, k) - w0;
-                    const int ik = __shfl_sync(0xffffffffu, rk.x + rk.z, k);   // first tile index
-                    const int t_lo = max(0, -ok), t_hi = min(lk, wn - ok);
-                    for (int t = t_lo + lane; t < t_hi; t += 32)
-                        flat[ok + t] = (uint16_t)((k << LJ_TILE_BITS) | (ik + t));
+                if (lane < 27) {
+                    // lane k writes its cell's part of the window: (k, tile index)
+                    const int ok = off - w0;
+                    const int t_lo = max(0, -ok), t_hi = min(len, wn - ok);
+                    const unsigned code = ((unsigned)lane << LJ_TILE_BITS) | (unsigned)(rk.x + rk.z);
+                    for (int t = t_lo; t < t_hi; ++t) flat[ok + t] = (uint16_t)(code + (unsigned)t);
                 }
                 __syncwarp();
                 // one candidate per lane, tested against the quad's particles;
@@ -490,13 +489,15 @@ __global__ void __launch_bounds__(LJ_LIST_THREADS, 3) k_nlist(BoxDev b)
                     const float qx = t < wn ? pj.x + sh.x : 1.0e38f;
                     const float qy = pj.y + sh.y, qz = pj.z + sh.z;
                     const uint32_t ent = (uint32_t)idx + kent[k];
+                    // tile slices are disjoint, so the index alone finds the
+                    // particle itself: quad slot idx - self13 (if in 0..3)
+                    const int selfg = idx - self13;
 #pragma unroll
                     for (int g = 0; g < 4; ++g) {
                         const float ddx = pq[g].x - qx, ddy = pq[g].y - qy, ddz = pq[g].z - qz;
                         const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                        // tile slices are disjoint, so the index alone finds the
-                        // particle itself; slots past the quad's end take nothing
-                        const bool in = r2 < hi2 && idx != self13 + g && g < nq;
+                        // slots past the quad's end take nothing
+                        const bool in = r2 < hi2 && selfg != g && g < nq;
                         nearb[g] = nearb[g] || (in && r2 >= lo2);
                         const unsigned bits = __ballot_sync(0xffffffffu, in);
                         const int pos = cnt[g] + __popc(bits & lt_mask);
