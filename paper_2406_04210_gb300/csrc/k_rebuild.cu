@@ -478,31 +478,48 @@ __global__ void __launch_bounds__(LJ_LIST_THREADS, 3) k_nlist(BoxDev b)
                 // one candidate per lane, tested against the quad's particles;
                 // pairs within the recheck band are kept here and settled in
                 // FP64 afterwards
-                for (int t0 = 0; t0 < wn; t0 += 32) {
-                    const int t = t0 + lane;
-                    const unsigned e = t < wn ? flat[t] : 0u;
-                    const int k = (int)(e >> LJ_TILE_BITS);
-                    const int idx = (int)(e & LJ_TILE_MASK);
-                    const float4 pj = s_tile[idx];
-                    const float4 sh = s_shift[k];
-                    // lanes past the window take a far point, whose r2 is inf
-                    const float qx = t < wn ? pj.x + sh.x : 1.0e38f;
-                    const float qy = pj.y + sh.y, qz = pj.z + sh.z;
-                    const uint32_t ent = (uint32_t)idx + kent[k];
-                    // tile slices are disjoint, so the index alone finds the
-                    // particle itself: quad slot idx - self13 (if in 0..3)
-                    const int selfg = idx - self13;
+                // two candidates per lane per pass (t and t + 32): two
+                // independent test-and-append chains for the scheduler
+                for (int t0 = 0; t0 < wn; t0 += 64) {
+                    float qx[2], qy[2], qz[2];
+                    uint32_t ent[2];
+                    int selfg[2];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int t = t0 + 32 * h + lane;
+                        const unsigned e = t < wn ? flat[t] : 0u;
+                        const int k = (int)(e >> LJ_TILE_BITS);
+                        const int idx = (int)(e & LJ_TILE_MASK);
+                        const float4 pj = s_tile[idx];
+                        const float4 sh = s_shift[k];
+                        // lanes past the window take a far point, whose r2 is inf
+                        qx[h] = t < wn ? pj.x + sh.x : 1.0e38f;
+                        qy[h] = pj.y + sh.y;
+                        qz[h] = pj.z + sh.z;
+                        ent[h] = (uint32_t)idx + kent[k];
+                        // tile slices are disjoint, so the index alone finds the
+                        // particle itself: quad slot idx - self13 (if in 0..3)
+                        selfg[h] = idx - self13;
+                    }
 #pragma unroll
                     for (int g = 0; g < 4; ++g) {
-                        const float ddx = pq[g].x - qx, ddy = pq[g].y - qy, ddz = pq[g].z - qz;
-                        const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                        // slots past the quad's end take nothing
-                        const bool in = r2 < hi2 && selfg != g && g < nq;
-                        nearb[g] = nearb[g] || (in && r2 >= lo2);
-                        const unsigned bits = __ballot_sync(0xffffffffu, in);
-                        const int pos = cnt[g] + __popc(bits & lt_mask);
-                        if (in && pos < b.K) row0[(size_t)b.K * g + pos] = ent;
-                        cnt[g] += __popc(bits);
+                        bool in[2];
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const float ddx = pq[g].x - qx[h], ddy = pq[g].y - qy[h], ddz = pq[g].z - qz[h];
+                            const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                            // slots past the quad's end take nothing
+                            in[h] = r2 < hi2 && selfg[h] != g && g < nq;
+                            nearb[g] = nearb[g] || (in[h] && r2 >= lo2);
+                        }
+                        const unsigned b0 = __ballot_sync(0xffffffffu, in[0]);
+                        const unsigned b1 = __ballot_sync(0xffffffffu, in[1]);
+                        const int pos0 = cnt[g] + __popc(b0 & lt_mask);
+                        const int pos1 = cnt[g] + __popc(b0) + __popc(b1 & lt_mask);
+                        uint32_t* const rg = row0 + (size_t)b.K * g;
+                        if (in[0] && pos0 < b.K) rg[pos0] = ent[0];
+                        if (in[1] && pos1 < b.K) rg[pos1] = ent[1];
+                        cnt[g] += __popc(b0) + __popc(b1);
                     }
                 }
             }
