@@ -90,7 +90,9 @@ __global__ void __launch_bounds__(LJ_CHUNK) k_bin(BoxDev b, int from_abs)
         int q[3];
         for (int c = 0; c < 3; ++c) {
             double L = R.L[c];
-            double f = floor(x[c] / L);
+            // floor(x / L); the FP64 division (slow on this GPU) only where
+            // the quotient can round to 1 or more, or x is negative
+            double f = (x[c] >= 0.0 && x[c] < R.wrap_hi[c]) ? 0.0 : floor(x[c] / L);
             if (f != 0.0) {
                 x[c] = x[c] - L * f;
                 im[c] += (int)f;

@@ -725,7 +725,10 @@ md_status md_batch_create(md_box** out, int32_t nrep, const int64_t* n, const do
     int64_t poff = 0, uoff = 0;
     for (int r = 0; r < nrep; ++r) {
         RepDev R{};
-        for (int c = 0; c < 3; ++c) R.L[c] = box[3 * r + c];
+        for (int c = 0; c < 3; ++c) {
+            R.L[c] = box[3 * r + c];
+            R.wrap_hi[c] = R.L[c] * (1.0 - std::ldexp(1.0, -50));
+        }
         R.p_off = (int)poff;
         R.n = (int)n[r];
         R.u_off = (int)uoff;

@@ -62,6 +62,7 @@
 
 struct RepDev {
     double L[3];
+    double wrap_hi[3];         // L (1 - 2^-50): 0 <= x < wrap_hi implies floor(x / L) = 0
     double ell[3];             // cell edge lengths
     double inv_ell[3];
     float ellf[3];
