@@ -248,6 +248,70 @@ def bench_batched(ljmd, inputs, steps):
             "value": tot * steps / (ms / 1e3), "unit": UNIT}
 
 
+def _guarded(fn):
+    """Run a secondary measurement; a failure is reported in its place
+    instead of ending the run."""
+    try:
+        return fn()
+    except Exception as e:  # noqa: BLE001 - reported, not hidden
+        return {"error": f"{type(e).__name__}: {e}"}
+
+
+def bench_drift(ljmd, inputs, steps):
+    """NVE energy drift of the N = 4000 fluid (fcc 10^3 x 4, rho 0.8442,
+    T 0.722, dt 0.005) over `steps` steps in each precision: the slope of a
+    linear fit of E/N against time (per particle per tau) and the largest
+    |E(t) - E(0)|/N, energies recorded every step."""
+    s = inputs.lj4000()
+    out = {"workload": f"fcc 10^3 x 4 = 4000 particles, rho 0.8442, T 0.722, dt 0.005, {steps} NVE steps "
+                       f"({steps * s.dt:g} tau), energies every step"}
+    t = (np.arange(steps) + 1) * s.dt
+    for prec in ("mixed_ds", "mixed_fp64", "fp64"):
+        b = ljmd.from_system(s, prec)
+        t0 = time.perf_counter()
+        th = b.integrate(s.dt, steps)
+        sec = time.perf_counter() - t0
+        b.close()
+        E = (th[:, 0, 0] + th[:, 0, 1]) / s.n
+        slope = float(np.polyfit(t, E - E[0], 1)[0])
+        out[prec] = {"drift_per_particle_per_tau": slope,
+                     "max_abs_dev_per_particle": float(np.abs(E - E[0]).max()),
+                     "E_per_particle_0": float(E[0]), "seconds": sec}
+    return out
+
+
+def bench_binary(ljmd, inputs, steps_mixed, steps_fp64):
+    """Binary LJ mixture 80:20 at rho 1.2, N = 256,000, dt 0.003: particle-
+    steps/s of the mixed path against the all-FP64 GPU path.  The random
+    insertion (minimum separation 0.7) is relaxed on the GPU first by 40
+    rounds of 10 MD steps with the velocities zeroed after each round; the
+    timed runs then start from the relaxed positions with Maxwell-Boltzmann
+    velocities at T = 0.7."""
+    s = inputs.binary_random_system(seed=inputs.SEEDS["binary256k"])
+    b = ljmd.from_system(s, "mixed_ds")
+    zero = np.zeros_like(s.vel)
+    b.set_state(s.pos, zero)
+    for _ in range(40):
+        b.integrate(s.dt, 10, thermo=False)
+        pos, _, _ = b.get_state()
+        b.set_state(pos, zero)
+    pos, _, _ = b.get_state()
+    b.close()
+    relaxed = inputs.System(s.box, pos, s.vel, s.type, s.eps, s.sigma, s.rcut, s.skin, s.dt, s.T, s.seed)
+    out = {"workload": "binary LJ 80:20, N = 256,000, rho 1.2, T 0.7, dt 0.003, rc 2.5 sigma_ab, skin 0.3, "
+                       "NVE, energies every step (random insertion relaxed on the GPU)"}
+    for prec, k in (("mixed_ds", steps_mixed), ("fp64", steps_fp64)):
+        bb = ljmd.from_system(relaxed, prec)
+        bb.integrate(s.dt, 20)
+        ms, _ = timed_call(lambda: bb.integrate(s.dt, k))
+        info = bb.info()
+        bb.close()
+        out[prec] = {"value": s.n * k / (ms / 1e3), "unit": UNIT, "steps": k, "ms_per_step": ms / k,
+                     "rebuilds": int(info.rebuilds)}
+    out["mixed_over_fp64"] = out["mixed_ds"]["value"] / out["fp64"]["value"]
+    return out
+
+
 def run_gpu(args):
     import torch
     from paper_2406_04210_gb300 import build, inputs, ljmd
@@ -341,6 +405,9 @@ def run_gpu(args):
 
     adj = None if args.quick else bench_adjoint(ljmd, inputs)
     batched = None if args.quick else bench_batched(ljmd, inputs, max(50, args.steps // 5))
+    drift = None if args.quick else _guarded(lambda: bench_drift(ljmd, inputs, 100000))
+    binary = None if args.quick else _guarded(lambda: bench_binary(ljmd, inputs, 10 * args.steps,
+                                                                     max(20, args.steps)))
 
     if rank != 0:
         if dist:
@@ -372,7 +439,8 @@ def run_gpu(args):
                    "drift_per_particle": float((E[-1] - E[0]) / n)},
         "rebuilds_in_timed_region": int(info1.rebuilds - info0.rebuilds),
         "adjoint_forward_ratio": adj["ratio"] if adj else None,
-        "adjoint": adj, "batched": batched, "tuning": tuning,
+        "adjoint": adj, "batched": batched, "drift_lj4000": drift, "binary256k": binary,
+        "tuning": tuning,
     }
     print(json.dumps(line), flush=True)
     if dist:
