@@ -312,6 +312,23 @@ def bench_binary(ljmd, inputs, steps_mixed, steps_fp64):
     return out
 
 
+def job_throughput(ms_local, n_local, steps, dist=None):
+    """Whole-job particle-steps/s over all ranks: the particles every rank
+    advanced (summed) times `steps`, over the slowest rank's time (max over
+    ranks).  Returns (value, ms_max).  Each rank runs its own box (replicas
+    only), so this is the one collective of a multi-GPU run."""
+    ms, n = float(ms_local), float(n_local)
+    if dist is not None and dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        import torch
+        dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        c = torch.tensor([n], dtype=torch.float64, device=dev)
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+        ms, n = float(t.item()), float(c.item())
+    return n * steps / (ms / 1e3), ms
+
+
 def run_gpu(args):
     import torch
     from paper_2406_04210_gb300 import build, inputs, ljmd
@@ -351,11 +368,7 @@ def run_gpu(args):
     prof = box.profile()
     launches = int(info1.launches - info0.launches)
     th = thermo[: args.steps].cpu().numpy()
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = n * world * args.steps / (ms / 1e3)
+    value, ms = job_throughput(ms, n, args.steps, dist)
 
     # roofline of the dominant kernel (pair force), timed in the graph
     f_ms, f_n = prof["force"]
