@@ -312,6 +312,33 @@ def bench_binary(ljmd, inputs, steps_mixed, steps_fp64):
     return out
 
 
+def bench_temperature_sweep(ljmd, inputs, steps, temps=(0.5, 0.722, 1.0, 1.5, 2.0, 3.0)):
+    """The truncated-force study of the paper (Sec. 5): N = 100,000, `steps`
+    NVE steps per temperature (rho 0.8442, rc 2.5, skin 0.3, dt 0.005).  Per
+    temperature: particle-steps/s (no phase events), list builds per step,
+    and the phase shares from a profiled run of steps / 10 (a hotter fluid
+    moves faster, so the lists are rebuilt more often)."""
+    out = {"workload": f"first 100,000 sites of an fcc lattice, rho 0.8442, rc 2.5, skin 0.3, dt 0.005, "
+                       f"{steps} NVE steps per temperature, energies every step", "points": []}
+    for T in temps:
+        s = inputs.fcc_subset_system(100000, 0.8442, T, inputs.SEEDS["lj4m"] + 7)
+        b = ljmd.from_system(s, "mixed_ds")
+        b.integrate(s.dt, 200)
+        i0 = b.info()
+        ms, _ = timed_call(lambda: b.integrate(s.dt, steps))
+        i1 = b.info()
+        b.set_profiling(True)
+        b.integrate(s.dt, max(100, steps // 10))
+        prof = b.profile()
+        b.close()
+        tot = sum(v[0] for v in prof.values()) or 1.0
+        out["points"].append({"T": T, "value": s.n * steps / (ms / 1e3), "unit": UNIT,
+                              "ms_per_step": ms / steps,
+                              "rebuilds_per_step": (i1.rebuilds - i0.rebuilds) / steps,
+                              "share": {k: v[0] / tot for k, v in prof.items()}})
+    return out
+
+
 def job_throughput(ms_local, n_local, steps, dist=None):
     """Whole-job particle-steps/s over all ranks: the particles every rank
     advanced (summed) times `steps`, over the slowest rank's time (max over
@@ -421,6 +448,7 @@ def run_gpu(args):
     drift = None if args.quick else _guarded(lambda: bench_drift(ljmd, inputs, 100000))
     binary = None if args.quick else _guarded(lambda: bench_binary(ljmd, inputs, 10 * args.steps,
                                                                      max(20, args.steps)))
+    tsweep = None if args.quick else _guarded(lambda: bench_temperature_sweep(ljmd, inputs, 50 * args.steps))
 
     if rank != 0:
         if dist:
@@ -453,6 +481,7 @@ def run_gpu(args):
         "rebuilds_in_timed_region": int(info1.rebuilds - info0.rebuilds),
         "adjoint_forward_ratio": adj["ratio"] if adj else None,
         "adjoint": adj, "batched": batched, "drift_lj4000": drift, "binary256k": binary,
+        "temperature_sweep": tsweep,
         "tuning": tuning,
     }
     print(json.dumps(line), flush=True)
