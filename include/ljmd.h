@@ -114,10 +114,32 @@ md_status md_box_destroy(md_box* b);
  * energy is shifted to zero at the cutoff.  The list radius is
  * rl = max(rcut) + skin; cells are floor(L/rl) per dimension.  Returns
  * MD_ERR_BOX_TOO_SMALL if rl >= L/2 for any replica.  Rebuilds the lists and
- * recomputes the forces at the current positions. */
+ * recomputes the forces at the current positions.
+ * All-pairs form (Sec. 4: the untruncated LJ interaction between all
+ * particles): every rcut = +INFINITY.  Forces then sum over every pair of a
+ * replica with the minimum image and no lists; the skin only sets how often
+ * positions are re-wrapped.  md_adjoint, md_pair_hist, md_get_nlist and
+ * md_autotune return MD_ERR_ARG in this form. */
 md_status md_set_lj(md_box* b, int32_t ntypes, const double* eps,
                     const double* sigma, const double* rcut, double skin,
                     int32_t energy_shift);
+
+/* Stochastic Andersen-like thermostat (Sec. 4: the "Boltzmann" thermostat of
+ * the all-to-all workload).  After the finalize half kick of every step of
+ * md_integrate, each particle collides with the heat bath with probability
+ * rate * dt; its velocity is then redrawn from the Maxwell-Boltzmann
+ * distribution at T_bath[r] of its replica (unit mass).  The random numbers
+ * are Philox4x32-10 (Salmon et al., SC'11) with key = seed + replica index
+ * and counter = (index of the particle inside its replica, step index low,
+ * step index high, 0 or 1); the step index counts the steps since this call.  Word 0 decides the collision (below
+ * floor(rate dt 2^32)); the three Gaussians come by Box-Muller from words 1,
+ * 2 and from words 0, 1 of the second counter.  Energies are taken after
+ * the collisions.  rate = 0 switches it off (the default: NVE).
+ *   T_bath  host, nrep entries (> 0), or NULL with rate = 0
+ * md_integrate with ckpt_every > 0 returns MD_ERR_ARG while it is on (the
+ * reverse of a stochastic collision is not defined). */
+md_status md_set_thermostat(md_box* b, const double* T_bath, double rate,
+                            uint64_t seed);
 
 /* Neighbour-list update (Sec. 3, Code structure; Sec. 5): re-bin and rebuild
  * the lists of every replica in which some particle moved more than skin/2

@@ -69,8 +69,14 @@ def lib():
             L.or_dforce_dparam.restype = ctypes.c_int32
             L.or_run.argtypes = [ctypes.c_int64, _D, ctypes.c_int32, _I32, _D, _D, _I32,
                                  _D, _D, _D, ctypes.c_int32, ctypes.c_double,
-                                 ctypes.c_double, ctypes.c_int64, _D, _D]
+                                 ctypes.c_double, ctypes.c_int64, _D, _D,
+                                 ctypes.c_double, ctypes.c_double, ctypes.c_uint64]
             L.or_run.restype = ctypes.c_int64
+            L.or_philox4x32.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+            L.or_philox4x32.restype = None
+            L.or_thermostat.argtypes = [ctypes.c_int64, _D, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_double, ctypes.c_uint64, ctypes.c_int64]
+            L.or_thermostat.restype = ctypes.c_int64
             L.or_hist.argtypes = [ctypes.c_int64, _D, _D, _I32, _I64, ctypes.c_int64,
                                   ctypes.c_double, ctypes.c_int32, ctypes.c_double,
                                   ctypes.c_double, _D]
@@ -224,8 +230,10 @@ def dforce_dparam(box, pos, lj: LJ, lam, type_=None, nl: NList | None = None):
     return ge, gs
 
 
-def run(box, pos, vel, lj: LJ, skin, dt, nsteps, type_=None, img=None, traj=False):
-    """Velocity-Verlet MD.  Returns dict(pos, vel, img, thermo, builds[, traj])."""
+def run(box, pos, vel, lj: LJ, skin, dt, nsteps, type_=None, img=None, traj=False, thermostat=None):
+    """Velocity-Verlet MD.  Returns dict(pos, vel, img, thermo, builds[, traj]).
+    thermostat = (T_bath, rate, seed): Andersen-like collisions after every
+    finalize (see or_thermostat).  Every lj.rcut infinite: all pairs, no lists."""
     pos = _f64(pos, (-1, 3)).copy()
     vel = _f64(vel, (-1, 3)).copy()
     n = pos.shape[0]
@@ -233,15 +241,34 @@ def run(box, pos, vel, lj: LJ, skin, dt, nsteps, type_=None, img=None, traj=Fals
     img = np.zeros((n, 3), dtype=np.int32) if img is None else np.array(img, dtype=np.int32)
     thermo = np.zeros((max(nsteps, 1), 4))
     tr = np.zeros((nsteps + 1, n, 3)) if traj else None
+    T_bath, rate, seed = thermostat if thermostat is not None else (0.0, 0.0, 0)
     b = lib().or_run(n, _d(_f64(box)), lj.ntypes, _i32(t), _d(pos), _d(vel), _i32(img),
                      _d(lj.eps), _d(lj.sigma), _d(lj.rcut), lj.shift, float(skin),
-                     float(dt), int(nsteps), _d(thermo), _d(tr) if traj else None)
+                     float(dt), int(nsteps), _d(thermo), _d(tr) if traj else None,
+                     float(T_bath), float(rate), ctypes.c_uint64(int(seed)))
     if b < 0:
         raise RuntimeError(f"oracle run failed ({b})")
     out = dict(pos=pos, vel=vel, img=img, thermo=thermo[:nsteps], builds=int(b))
     if traj:
         out["traj"] = tr
     return out
+
+
+def philox4x32(ctr, key):
+    """Philox4x32-10 of one 4-word counter and 2-word key (uint32)."""
+    c = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint32))
+    k = np.ascontiguousarray(np.asarray(key, dtype=np.uint32))
+    o = np.zeros(4, dtype=np.uint32)
+    lib().or_philox4x32(c.ctypes.data, k.ctypes.data, o.ctypes.data)
+    return o
+
+
+def thermostat(vel, T_bath, rate, dt, seed, step):
+    """One thermostat application to a copy of vel; returns (vel, collisions)."""
+    v = _f64(vel, (-1, 3)).copy()
+    hits = lib().or_thermostat(v.shape[0], _d(v), float(T_bath), float(rate), float(dt),
+                               ctypes.c_uint64(int(seed)), int(step))
+    return v, int(hits)
 
 
 def hist(box, pos, nbins=64, rhist=2.5, w=None, rmax_pairs=2.8):

@@ -35,6 +35,16 @@
  *   or_hist, or_hist_grad   normalisation sum and central differences
  *   or_adjoint              central differences of a trajectory loss
  *   or_fire                 monotone descent to max|F| < ftol (input relaxation)
+ *   or_philox4x32           uniformity and stream independence (chi-square),
+ *                           Gaussian moments of the Box-Muller draws
+ *   or_run with a thermostat  collision frequency = rate dt (binomial), canonical
+ *                           <E_kin> = 3/2 (N - 1) T, velocity distribution
+ *   or_run, all pairs       forces == or_forces_brute with rc = inf, NVE drift
+ *
+ * The all-to-all workload (Sec. 4: untruncated LJ forces between all pairs,
+ * velocity-Verlet, and a stochastic Andersen-like "Boltzmann" thermostat) is
+ * or_run with every cutoff infinite: forces by brute force over all pairs
+ * with the minimum image, no lists.
  */
 #include <math.h>
 #include <stdint.h>
@@ -133,6 +143,84 @@ int32_t or_forces_brute(int64_t n, const double L[3], int32_t nt,
     if (epot) *epot = e;
     if (virial) *virial = w;
     return OR_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: */
+/* as easy as 1, 2, 3", SC'11): a counter-based generator.  Each of the  */
+/* ten rounds multiplies words 0 and 2 of the counter by two fixed odd   */
+/* constants, swaps the high/low halves across the words and mixes in   */
+/* the key; the key advances by two Weyl constants between rounds.      */
+/* ------------------------------------------------------------------ */
+void or_philox4x32(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    uint32_t c[4] = {ctr_in[0], ctr_in[1], ctr_in[2], ctr_in[3]};
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c[0];
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c[2];
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c[1] ^ k0;
+        uint32_t n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = lo1;
+        c[2] = n2;
+        c[3] = lo0;
+    }
+    for (int i = 0; i < 4; ++i) out[i] = c[i];
+}
+
+/* Uniform in (0, 1) from a 32-bit word: (x + 1/2) / 2^32.              */
+static double u01(uint32_t x) { return ((double)x + 0.5) * (1.0 / 4294967296.0); }
+
+/* ------------------------------------------------------------------ */
+/* Andersen-like ("Boltzmann") thermostat, applied after the finalize   */
+/* half kick of step s (reading of Sec. 4, which names the thermostat   */
+/* only).  Particle u (user index) collides with the bath when word 0   */
+/* of philox(ctr = (u, s lo, s hi, 0), key = seed) is below             */
+/* floor(rate dt 2^32); its velocity is then redrawn from the           */
+/* Maxwell-Boltzmann distribution at T_bath (unit mass): three          */
+/* Gaussians by Box-Muller, g0, g1 from words 1, 2 and g2 from words    */
+/* 0, 1 of philox(ctr = (u, s lo, s hi, 1)), v = sqrt(T_bath) g.        */
+/* Returns the number of collisions.                                    */
+/* ------------------------------------------------------------------ */
+static uint32_t collide_threshold(double rate, double dt)
+{
+    double t = floor(rate * dt * 4294967296.0);
+    if (!(t > 0.0)) return 0u;
+    if (t >= 4294967295.0) return 4294967295u;
+    return (uint32_t)t;
+}
+
+int64_t or_thermostat(int64_t n, double* vel, double T_bath, double rate, double dt,
+                      uint64_t seed, int64_t step)
+{
+    const uint32_t thr = collide_threshold(rate, dt);
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    const double sd = sqrt(T_bath);
+    const double two_pi = 6.283185307179586476925286766559;
+    int64_t hits = 0;
+    for (int64_t u = 0; u < n; ++u) {
+        uint32_t c[4] = {(uint32_t)u, (uint32_t)step, (uint32_t)((uint64_t)step >> 32), 0u};
+        uint32_t x[4];
+        or_philox4x32(c, key, x);
+        if (!(x[0] < thr)) continue;
+        c[3] = 1u;
+        uint32_t y[4];
+        or_philox4x32(c, key, y);
+        double r1 = sqrt(-2.0 * log(u01(x[1]))), a1 = two_pi * u01(x[2]);
+        double r2 = sqrt(-2.0 * log(u01(y[0]))), a2 = two_pi * u01(y[1]);
+        vel[3 * u + 0] = sd * (r1 * cos(a1));
+        vel[3 * u + 1] = sd * (r1 * sin(a1));
+        vel[3 * u + 2] = sd * (r2 * cos(a2));
+        ++hits;
+    }
+    return hits;
 }
 
 /* ------------------------------------------------------------------ */
@@ -368,15 +456,19 @@ static int64_t build_list(int64_t n, const double L[3], const double* pos,
     }
 }
 
+/* Thermostat (rate > 0): or_thermostat after the finalize of step s,  */
+/* s = 0, 1, ...; energies are taken after it.  Every cutoff infinite:  */
+/* the all-to-all form, forces by brute force over all pairs.          */
 int64_t or_run(int64_t n, const double L[3], int32_t nt, const int32_t* type,
                double* pos, double* vel, int32_t* img, const double* eps,
                const double* sigma, const double* rcut, int32_t shift,
                double skin, double dt, int64_t nsteps, double* thermo,
-               double* traj)
+               double* traj, double T_bath, double rate, uint64_t seed)
 {
     double rl = max_rcut(nt, rcut) + skin;
+    const int all_pairs = isinf(rl);
     for (int c = 0; c < 3; ++c)
-        if (!(rl < 0.5 * L[c])) return -OR_ERR_BOX;
+        if (!all_pairs && !(rl < 0.5 * L[c])) return -OR_ERR_BOX;
     int64_t cap = 64;
     int32_t* count = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n + 1));
     int64_t* list = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n * cap + 1));
@@ -386,10 +478,14 @@ int64_t or_run(int64_t n, const double L[3], int32_t nt, const int32_t* type,
     int64_t builds = 0;
     double e = 0.0, w = 0.0;
 
-    if (build_list(n, L, pos, rl, &count, &list, &cap) < 0) return -OR_ERR_OOM;
-    ++builds;
-    or_forces_list(n, L, nt, type, pos, eps, sigma, rcut, shift, count, list,
-                   cap, f, &e, &w);
+    if (all_pairs) {
+        or_forces_brute(n, L, nt, type, pos, eps, sigma, rcut, shift, f, &e, &w);
+    } else {
+        if (build_list(n, L, pos, rl, &count, &list, &cap) < 0) return -OR_ERR_OOM;
+        ++builds;
+        or_forces_list(n, L, nt, type, pos, eps, sigma, rcut, shift, count, list,
+                       cap, f, &e, &w);
+    }
     if (traj) memcpy(traj, pos, sizeof(double) * (size_t)(3 * n));
 
     for (int64_t s = 0; s < nsteps; ++s) {
@@ -412,20 +508,24 @@ int64_t or_run(int64_t n, const double L[3], int32_t nt, const int32_t* type,
                         disp[3 * i + 2] * disp[3 * i + 2];
             if (d2 > dmax2) dmax2 = d2;
         }
-        if (dmax2 > 0.25 * skin * skin) {
+        if (!all_pairs && dmax2 > 0.25 * skin * skin) {
             if (build_list(n, L, pos, rl, &count, &list, &cap) < 0)
                 return -OR_ERR_OOM;
             ++builds;
             memset(disp, 0, sizeof(double) * (size_t)(3 * n));
         }
         /* force */
-        or_forces_list(n, L, nt, type, pos, eps, sigma, rcut, shift, count,
-                       list, cap, f, &e, &w);
+        if (all_pairs)
+            or_forces_brute(n, L, nt, type, pos, eps, sigma, rcut, shift, f, &e, &w);
+        else
+            or_forces_list(n, L, nt, type, pos, eps, sigma, rcut, shift, count,
+                           list, cap, f, &e, &w);
         /* finalize: half kick */
         double ek = 0.0;
         for (int64_t k = 0; k < 3 * n; ++k) {
             vel[k] = vel[k] + 0.5 * dt * f[k];
         }
+        if (rate > 0.0) or_thermostat(n, vel, T_bath, rate, dt, seed, s);
         for (int64_t i = 0; i < n; ++i)
             ek += 0.5 * ((vel[3 * i] * vel[3 * i] + vel[3 * i + 1] * vel[3 * i + 1]) +
                          vel[3 * i + 2] * vel[3 * i + 2]);

@@ -283,6 +283,176 @@ __global__ void __launch_bounds__(LJ_F64_THREADS) k_force_f64(BoxDev b)
     }
 }
 
+// ---------------------------------------------------------------------------
+// All pairs (Sec. 4: the untruncated LJ interaction between all particles;
+// every cutoff infinite).  One 128-particle chunk per block pass, LJ_TPP
+// threads per particle.  The replica's offsets are staged through shared
+// memory in tiles of kAllTile and thread l of a particle takes the tile's
+// entries l, l + LJ_TPP, ...  With one cell per replica all offsets are
+// from the box centre: d = o_i - o_j - L rint((o_i - o_j) / L) is the
+// minimum image.
+// ---------------------------------------------------------------------------
+constexpr int kAllTile = 1024;
+constexpr int kAllThreads = LJ_CHUNK * LJ_TPP;
+
+template <bool MONO, bool ENERGY>
+__global__ void __launch_bounds__(kAllThreads) k_force_all_f32(BoxDev b)
+{
+    __shared__ float4 s_pos[kAllTile];
+    __shared__ float4 s_lj[LJ_MAXT * LJ_MAXT];   // c12, c6, e12, e6
+    __shared__ float s_esh[LJ_MAXT * LJ_MAXT];
+    __shared__ double s_red[2][32];
+    const LJDev* lj = b.lj;
+    const int nt = lj->nt;
+    for (int k = threadIdx.x; k < nt * nt; k += blockDim.x) {
+        s_lj[k] = make_float4(lj->c12[k], lj->c6[k], lj->e12[k], lj->e6[k]);
+        s_esh[k] = lj->shift[k];
+    }
+    const float4 mlj = make_float4(lj->c12[0], lj->c6[0], lj->e12[0], lj->e6[0]);
+    const float mesh = lj->shift[0];
+    const int grp = threadIdx.x / LJ_TPP, l4 = threadIdx.x % LJ_TPP;
+    for (int w = blockIdx.x; w < b.nchunk; w += gridDim.x) {
+        const int4 ch = b.chunk[w];
+        const RepDev& R = b.rep[ch.x];
+        const float Lx = (float)R.L[0], Ly = (float)R.L[1], Lz = (float)R.L[2];
+        const float ix = (float)(1.0 / R.L[0]), iy = (float)(1.0 / R.L[1]), iz = (float)(1.0 / R.L[2]);
+        const int p = ch.y + grp;
+        const bool act = p < ch.z;
+        const float4 pi = b.posq[act ? p : ch.y];
+        const int tb = __float_as_int(pi.w) * nt;
+        float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f, vir = 0.f;
+        const int j0 = R.p_off, j1 = R.p_off + R.n;
+        for (int t0 = j0; t0 < j1; t0 += kAllTile) {
+            const int nj = min(kAllTile, j1 - t0);
+            __syncthreads();   // the previous tile is no longer read
+            for (int t = threadIdx.x; t < nj; t += blockDim.x) s_pos[t] = b.posq[t0 + t];
+            __syncthreads();
+            for (int t = l4; t < nj; t += LJ_TPP) {
+                const float4 pj = s_pos[t];
+                float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+                dx -= Lx * rintf(dx * ix);
+                dy -= Ly * rintf(dy * iy);
+                dz -= Lz * rintf(dz * iz);
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                float4 c;
+                float esh;
+                if (MONO) {
+                    c = mlj;
+                    esh = mesh;
+                } else {
+                    const int pp = tb + __float_as_int(pj.w);
+                    c = s_lj[pp];
+                    esh = ENERGY ? s_esh[pp] : 0.f;
+                }
+                const float r2i = __fdividef(1.0f, r2);
+                const float r6i = r2i * r2i * r2i;
+                float f = r2i * r6i * fmaf(c.x, r6i, -c.y);
+                const bool in = act && t0 + t != p;
+                f = in ? f : 0.f;
+                fx = fmaf(f, dx, fx);
+                fy = fmaf(f, dy, fy);
+                fz = fmaf(f, dz, fz);
+                if (ENERGY) {
+                    const float u = r6i * fmaf(c.z, r6i, -c.w) - esh;
+                    e += in ? u : 0.f;
+                    vir = fmaf(f, r2, vir);
+                }
+            }
+        }
+#pragma unroll
+        for (int o = LJ_TPP / 2; o > 0; o >>= 1) {
+            fx += __shfl_xor_sync(0xffffffffu, fx, o);
+            fy += __shfl_xor_sync(0xffffffffu, fy, o);
+            fz += __shfl_xor_sync(0xffffffffu, fz, o);
+        }
+        if (act && l4 == 0) {
+            b.force4[p] = make_float4(fx, fy, fz, 0.f);
+            if (!isfinite(fx + fy + fz)) atomicOr(&b.err[0], LJ_ERRBIT_NONFINITE);
+        }
+        if (ENERGY) {
+            double de = 0.5 * (double)e, dw = 0.5 * (double)vir;
+            block_sum2(de, dw, s_red);
+            if (threadIdx.x == 0) {
+                b.part_f[2 * w] = de;
+                b.part_f[2 * w + 1] = dw;
+            }
+        }
+    }
+}
+
+// All pairs in FP64 (MD_PREC_FP64), one thread per particle, FP64 offsets
+// staged through shared memory.
+template <bool ENERGY>
+__global__ void __launch_bounds__(LJ_CHUNK) k_force_all_f64(BoxDev b)
+{
+    constexpr int kT = 512;
+    __shared__ double s_x[kT], s_y[kT], s_z[kT];
+    __shared__ int s_t[kT];
+    __shared__ double s_red[2][32];
+    const LJDev* lj = b.lj;
+    const int nt = lj->nt;
+    const int np = b.np;
+    for (int w = blockIdx.x; w < b.nchunk; w += gridDim.x) {
+        const int4 ch = b.chunk[w];
+        const RepDev& R = b.rep[ch.x];
+        const double Lx = R.L[0], Ly = R.L[1], Lz = R.L[2];
+        const double ix = 1.0 / Lx, iy = 1.0 / Ly, iz = 1.0 / Lz;
+        const int p = ch.y + (int)threadIdx.x;
+        const bool act = p < ch.z;
+        const int pa = act ? p : ch.y;
+        const double xi = b.off[pa], yi = b.off[np + pa], zi = b.off[2 * np + pa];
+        const int ti = b.type[pa];
+        double fx = 0.0, fy = 0.0, fz = 0.0, e = 0.0, vir = 0.0;
+        const int j0 = R.p_off, j1 = R.p_off + R.n;
+        for (int t0 = j0; t0 < j1; t0 += kT) {
+            const int nj = min(kT, j1 - t0);
+            __syncthreads();
+            for (int t = threadIdx.x; t < nj; t += blockDim.x) {
+                s_x[t] = b.off[t0 + t];
+                s_y[t] = b.off[np + t0 + t];
+                s_z[t] = b.off[2 * np + t0 + t];
+                s_t[t] = b.type[t0 + t];
+            }
+            __syncthreads();
+            if (!act) continue;
+            for (int t = 0; t < nj; ++t) {
+                if (t0 + t == p) continue;
+                double dx = xi - s_x[t], dy = yi - s_y[t], dz = zi - s_z[t];
+                dx -= Lx * rint(dx * ix);
+                dy -= Ly * rint(dy * iy);
+                dz -= Lz * rint(dz * iz);
+                const double r2 = dx * dx + dy * dy + dz * dz;
+                const int pp = ti * nt + s_t[t];
+                const double r2i = 1.0 / r2;
+                const double s2 = lj->dsig2[pp] * r2i;
+                const double s6 = s2 * s2 * s2;
+                const double f = lj->deps48[pp] * r2i * s6 * (s6 - 0.5);
+                fx += f * dx;
+                fy += f * dy;
+                fz += f * dz;
+                if (ENERGY) {
+                    e += lj->deps4[pp] * s6 * (s6 - 1.0) - lj->dshift[pp];
+                    vir += f * r2;
+                }
+            }
+        }
+        if (act) {
+            b.force64[p] = fx;
+            b.force64[np + p] = fy;
+            b.force64[2 * np + p] = fz;
+            if (!isfinite(fx + fy + fz)) atomicOr(&b.err[0], LJ_ERRBIT_NONFINITE);
+        }
+        if (ENERGY) {
+            double de = 0.5 * e, dw = 0.5 * vir;
+            block_sum2(de, dw, s_red);
+            if (threadIdx.x == 0) {
+                b.part_f[2 * w] = de;
+                b.part_f[2 * w + 1] = dw;
+            }
+        }
+    }
+}
+
 // E_pot, E_kin, W, T per replica from the per-chunk partial sums, in a
 // fixed order (deterministic): each block sums one item (a run of up to 256
 // chunks of one replica) and stores its 3 sums; the block that completes a
@@ -357,6 +527,19 @@ __global__ void __launch_bounds__(256) k_thermo(BoxDev b, double* out, int with_
 
 cudaError_t launch_force(const BoxDev& b, int energy, Launch l)
 {
+    if (b.all_pairs) {
+        if (b.prec == 2) {
+            if (energy) k_force_all_f64<true><<<l.grid, LJ_CHUNK, 0, l.s>>>(b);
+            else k_force_all_f64<false><<<l.grid, LJ_CHUNK, 0, l.s>>>(b);
+        } else if (b.nt == 1) {
+            if (energy) k_force_all_f32<true, true><<<l.grid, kAllThreads, 0, l.s>>>(b);
+            else k_force_all_f32<true, false><<<l.grid, kAllThreads, 0, l.s>>>(b);
+        } else {
+            if (energy) k_force_all_f32<false, true><<<l.grid, kAllThreads, 0, l.s>>>(b);
+            else k_force_all_f32<false, false><<<l.grid, kAllThreads, 0, l.s>>>(b);
+        }
+        return cudaGetLastError();
+    }
     if (b.prec == 2) {
         if (energy) k_force_f64<true><<<l.grid, LJ_F64_THREADS, 0, l.s>>>(b);
         else k_force_f64<false><<<l.grid, LJ_F64_THREADS, 0, l.s>>>(b);

@@ -23,8 +23,34 @@ __device__ __forceinline__ double warp_sum_d(double v)
     return v;
 }
 
+// Andersen-like collision of particle p after the finalize of step `step`
+// (see md_set_thermostat): true and the new velocity in g when word 0 of
+// philox((local user index, step lo, step hi, 0), seed + replica) is below
+// the threshold; Gaussians by Box-Muller.
+__device__ __forceinline__ bool tstat_collide(const BoxDev& b, const RepDev& R, int r, int p, long long step,
+                                              double g[3])
+{
+    const unsigned u = (unsigned)(b.uid[p] - R.u_off);
+    const unsigned long long key = b.tstat_seed + (unsigned long long)r;
+    const uint2 k = make_uint2((unsigned)key, (unsigned)(key >> 32));
+    const unsigned slo = (unsigned)step, shi = (unsigned)((unsigned long long)step >> 32);
+    const uint4 x = philox4x32_10(make_uint4(u, slo, shi, 0u), k);
+    if (!(x.x < b.tstat_thr)) return false;
+    const uint4 y = philox4x32_10(make_uint4(u, slo, shi, 1u), k);
+    const double sd = sqrt(b.tstat_T[r]);
+    const double two_pi = 6.283185307179586476925286766559;
+    const double inv32 = 1.0 / 4294967296.0;
+    const double r1 = sqrt(-2.0 * log(((double)x.y + 0.5) * inv32)), a1 = two_pi * (((double)x.z + 0.5) * inv32);
+    const double r2 = sqrt(-2.0 * log(((double)y.x + 0.5) * inv32)), a2 = two_pi * (((double)y.y + 0.5) * inv32);
+    g[0] = sd * (r1 * cos(a1));
+    g[1] = sd * (r1 * sin(a1));
+    g[2] = sd * (r2 * cos(a2));
+    return true;
+}
+
+// sidx: this launch finalizes step (*b.step_ctr + sidx) (MID and LAST modes).
 template <int ACC, bool FORCE64, int MODE, bool ENERGY>
-__global__ void __launch_bounds__(LJ_CHUNK) k_integrate(BoxDev b, double dt)
+__global__ void __launch_bounds__(LJ_CHUNK) k_integrate(BoxDev b, double dt, int sidx)
 {
     __shared__ double s_red[LJ_CHUNK / 32];
     const int np = b.np;
@@ -53,6 +79,11 @@ __global__ void __launch_bounds__(LJ_CHUNK) k_integrate(BoxDev b, double dt)
                 F[2] = f4.z;
             }
             float o[3];
+            // thermostat collision after the finalize of this step
+            double g[3] = {0.0, 0.0, 0.0};
+            bool hit = false;
+            if (MODE != LJ_STEP_FIRST && b.tstat_thr)
+                hit = tstat_collide(b, b.rep[r], r, p, *b.step_ctr + sidx, g);
             if (ACC == 0) {
                 float ekf = 0.f;
 #pragma unroll
@@ -61,6 +92,7 @@ __global__ void __launch_bounds__(LJ_CHUNK) k_integrate(BoxDev b, double dt)
                     float inc = hdt_f * (float)F[c];
                     if (MODE != LJ_STEP_FIRST) {
                         ds_add_f(vh, vl, inc);
+                        if (hit) ds_from_double(g[c], vh, vl);
                         if (ENERGY) ekf += vh * vh;
                     }
                     if (MODE != LJ_STEP_LAST) {
@@ -83,6 +115,7 @@ __global__ void __launch_bounds__(LJ_CHUNK) k_integrate(BoxDev b, double dt)
                     double v = b.vel[c * np + p];
                     if (MODE != LJ_STEP_FIRST) {
                         v = v + hdt * F[c];
+                        if (hit) v = g[c];
                         if (ENERGY) ek += v * v;
                     }
                     if (MODE != LJ_STEP_LAST) {
@@ -125,9 +158,9 @@ __global__ void __launch_bounds__(LJ_CHUNK) k_integrate(BoxDev b, double dt)
 }
 
 template <int ACC, bool FORCE64>
-cudaError_t launch_integrate_t(const BoxDev& b, int mode, int energy, double dt, Launch l)
+cudaError_t launch_integrate_t(const BoxDev& b, int mode, int energy, double dt, int sidx, Launch l)
 {
-#define LJ_INT_CASE(M, E) k_integrate<ACC, FORCE64, M, E><<<l.grid, LJ_CHUNK, 0, l.s>>>(b, dt)
+#define LJ_INT_CASE(M, E) k_integrate<ACC, FORCE64, M, E><<<l.grid, LJ_CHUNK, 0, l.s>>>(b, dt, sidx)
     if (mode == LJ_STEP_FIRST) LJ_INT_CASE(LJ_STEP_FIRST, false);
     else if (mode == LJ_STEP_MID) {
         if (energy) LJ_INT_CASE(LJ_STEP_MID, true);
@@ -265,11 +298,24 @@ __global__ void __launch_bounds__(LJ_CHUNK) k_get_nlist(BoxDev b, int* count, lo
 
 }  // namespace
 
-cudaError_t launch_integrate(const BoxDev& b, int mode, int energy, double dt, Launch l)
+cudaError_t launch_integrate(const BoxDev& b, int mode, int energy, double dt, int sidx, Launch l)
 {
-    if (b.prec == 0) return launch_integrate_t<0, false>(b, mode, energy, dt, l);
-    if (b.prec == 1) return launch_integrate_t<1, false>(b, mode, energy, dt, l);
-    return launch_integrate_t<1, true>(b, mode, energy, dt, l);
+    if (b.prec == 0) return launch_integrate_t<0, false>(b, mode, energy, dt, sidx, l);
+    if (b.prec == 1) return launch_integrate_t<1, false>(b, mode, energy, dt, sidx, l);
+    return launch_integrate_t<1, true>(b, mode, energy, dt, sidx, l);
+}
+
+namespace {
+__global__ void k_step_advance(long long* ctr, long long n)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) *ctr += n;
+}
+}  // namespace
+
+cudaError_t launch_step_advance(long long* ctr, long long n, cudaStream_t s)
+{
+    k_step_advance<<<1, 32, 0, s>>>(ctr, n);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_upload(const BoxDev& b, const double* pos, const double* vel, const int* type,

@@ -98,6 +98,11 @@ struct md_box {
     // graphs
     std::vector<GraphEnt> graphs;
     int64_t chunk_steps = 100;
+    // all-pairs form and thermostat
+    bool all_pairs = false;
+    double tstat_rate = 0.0;
+    double* d_tstat_T = nullptr;
+    long long* d_step_ctr = nullptr;
     // tuning
     int min_capacity = 0;
     bool autofit = false;      // fit the capacity after the next full build
@@ -305,6 +310,10 @@ md_status enqueue_rebuild(md_box* b, int from_abs)
     CK(b, launch_scan_tiles(b->d, b->d_tiles, (int)b->tiles.size(), b->d_tile_sum, lt));
     CK(b, launch_scatter(b->d, l));
     CK(b, launch_sortgather(b->d, lcell(b)));
+    if (b->all_pairs) {
+        b->launches += 5;   // all pairs: binning only re-wraps and re-centres
+        return MD_OK;
+    }
     CK(b, launch_nlist(b->d, llist(b)));
     b->launches += 6;
     return MD_OK;
@@ -431,6 +440,7 @@ md_status snapshot_setup(md_box* b)
     b->snap_src.push_back({b->d.uid, sizeof(int) * (size_t)np});
     b->snap_src.push_back({b->d.type, sizeof(int) * (size_t)np});
     b->snap_src.push_back({b->d.cell, sizeof(int) * (size_t)np});
+    b->snap_src.push_back({b->d_step_ctr, sizeof(long long)});
     size_t tot = 0;
     for (auto& s : b->snap_src) tot += (s.second + 255) & ~(size_t)255;
     if (b->snap_bytes < tot) {
@@ -507,7 +517,7 @@ md_status enqueue_steps(md_box* b, int64_t n, double dt, int energy, double* rin
     for (int64_t s = 0; s <= n; ++s) {
         int mode = s == 0 ? LJ_STEP_FIRST : (s == n ? LJ_STEP_LAST : LJ_STEP_MID);
         CK(b, mark(s, 0, 0));
-        CK(b, launch_integrate(b->d, mode, s == 0 ? 0 : energy, dt, l));
+        CK(b, launch_integrate(b->d, mode, s == 0 ? 0 : energy, dt, (int)(s > 0 ? s - 1 : 0), l));
         CK(b, mark(s, 0, 1));
         b->launches += 1;
         if (s > 0 && energy) {
@@ -525,6 +535,11 @@ md_status enqueue_steps(md_box* b, int64_t n, double dt, int energy, double* rin
         CK(b, mark(s, 2, 1));
         b->launches += 1;
         if (tape) CKS(tape_save(b, (int)s + 1));
+    }
+    // steps since md_set_thermostat (the thermostat's counter), on the device
+    if (!tape) {
+        CK(b, launch_step_advance(b->d.step_ctr, n, b->stream));
+        b->launches += 1;
     }
     return MD_OK;
 }
@@ -787,6 +802,11 @@ md_status md_batch_create(md_box** out, int32_t nrep, const int64_t* n, const do
         CKS(dev_alloc(b, &d.disp_max, nrep));
         CKS(dev_alloc(b, &d.rebuild_req, nrep));
         CKS(dev_alloc(b, &d.any_req, 1));
+        CKS(dev_alloc(b, &b->d_step_ctr, 1));
+        d.step_ctr = b->d_step_ctr;
+        CKS(dev_alloc(b, &b->d_tstat_T, nrep));
+        d.tstat_T = b->d_tstat_T;
+        d.tstat_thr = 0u;
         CKS(dev_alloc(b, &d.nbuild, nrep));
         CKS(dev_alloc(b, &d.err, 4));
         CKS(dev_alloc(b, &d.part_k, std::max<size_t>(1, b->chunks.size())));
@@ -848,18 +868,23 @@ md_status md_set_lj(md_box* b, int32_t ntypes, const double* eps, const double* 
         return fail(b, MD_ERR_ARG, "md_set_lj: bad arguments");
     int nt = ntypes;
     double rcmax = 0.0;
+    int ninf = 0;
     for (int a = 0; a < nt; ++a)
         for (int c = 0; c < nt; ++c) {
             int k = a * nt + c, t = c * nt + a;
             if (!(eps[k] > 0) || !(sigma[k] > 0) || !(rcut[k] > 0) || eps[k] != eps[t] ||
-                sigma[k] != sigma[t] || rcut[k] != rcut[t])
+                sigma[k] != sigma[t] || rcut[k] != rcut[t] || std::isnan(rcut[k]))
                 return fail(b, MD_ERR_ARG, "md_set_lj: parameters must be positive and symmetric");
             rcmax = std::max(rcmax, rcut[k]);
+            ninf += std::isinf(rcut[k]) ? 1 : 0;
         }
+    if (ninf != 0 && ninf != nt * nt)
+        return fail(b, MD_ERR_ARG, "md_set_lj: cutoffs must be all finite or all infinite (all pairs)");
+    const bool all_pairs = ninf != 0;
     double rl = rcmax + skin;
     for (int r = 0; r < b->nrep; ++r)
         for (int c = 0; c < 3; ++c)
-            if (!(rl < 0.5 * b->reps[r].L[c]))
+            if (!all_pairs && !(rl < 0.5 * b->reps[r].L[c]))
                 return fail(b, MD_ERR_BOX_TOO_SMALL, "md_set_lj: rc + skin >= L/2");
     CKS(enter(b));
     // types given at creation must be < ntypes: checked on the host copy
@@ -873,7 +898,9 @@ md_status md_set_lj(md_box* b, int32_t ntypes, const double* eps, const double* 
     }
     // new cell grid: if it changes while particles are binned, put positions
     // back into xabs first
-    bool grid_changes = !b->lj_set || rl != b->rl;
+    bool grid_changes = !b->lj_set || rl != b->rl || all_pairs != b->all_pairs;
+    b->all_pairs = all_pairs;
+    b->d.all_pairs = all_pairs ? 1 : 0;
     if (b->lj_set && grid_changes && !b->fresh_abs) {
         CK(b, launch_materialize(b->d, lch(b)));
         b->fresh_abs = true;
@@ -974,8 +1001,8 @@ md_status md_set_lj(md_box* b, int32_t ntypes, const double* eps, const double* 
                               cudaMemcpyHostToDevice, b->stream));
         CKS(make_segments(b, false));
         // list capacity: expected neighbours at the densest replica, +30 %
-        double expect = maxdens * 4.18879020478639 * rl * rl * rl;
-        int K = round_up((int64_t)(1.3 * expect) + 16, 8);
+        double expect = all_pairs ? 0.0 : maxdens * 4.18879020478639 * rl * rl * rl;
+        int K = round_up((int64_t)(1.3 * expect) + 16, 8);   // all pairs: no lists, a token row
         if (b->min_capacity > 0) K = round_up(b->min_capacity, 8);
         CKS(alloc_lists(b, K));
         b->autofit = true;
@@ -984,6 +1011,27 @@ md_status md_set_lj(md_box* b, int32_t ntypes, const double* eps, const double* 
     b->rec_valid = false;
     CKS(full_rebuild(b));
     CKS(leave(b));
+    return MD_OK;
+}
+
+md_status md_set_thermostat(md_box* b, const double* T_bath, double rate, uint64_t seed)
+{
+    if (!b || !(rate >= 0.0) || !std::isfinite(rate) || (rate > 0.0 && !T_bath))
+        return fail(b, MD_ERR_ARG, "md_set_thermostat: bad arguments");
+    if (rate > 0.0)
+        for (int r = 0; r < b->nrep; ++r)
+            if (!(T_bath[r] > 0.0) || !std::isfinite(T_bath[r]))
+                return fail(b, MD_ERR_ARG, "md_set_thermostat: T_bath must be positive");
+    CKS(enter(b));
+    if (rate > 0.0)
+        CK(b, cudaMemcpyAsync(b->d_tstat_T, T_bath, sizeof(double) * b->nrep, cudaMemcpyHostToDevice, b->stream));
+    CK(b, cudaMemsetAsync(b->d_step_ctr, 0, sizeof(long long), b->stream));   // step index restarts at 0
+    b->tstat_rate = rate;
+    b->d.tstat_seed = seed;
+    b->d.tstat_thr = 0u;   // set per dt by md_integrate
+    b->rec_valid = false;
+    invalidate_graphs(b);
+    CKS(leave(b));   // T_bath may be pageable host memory
     return MD_OK;
 }
 
@@ -1046,7 +1094,18 @@ md_status md_integrate(md_box* b, double dt, int64_t nsteps, int32_t ckpt_every,
     if (ckpt_every > 0 && nsteps % ckpt_every != 0)
         return fail(b, MD_ERR_ARG, "md_integrate: nsteps must be a multiple of ckpt_every");
     if (nsteps == 0) return MD_OK;
+    if (ckpt_every > 0 && b->tstat_rate > 0.0)
+        return fail(b, MD_ERR_ARG, "md_integrate: no recorded run with the thermostat on");
     CKS(enter(b));
+    {
+        // collision threshold of this dt: floor(rate dt 2^32), as a 32-bit word
+        double t = std::floor(b->tstat_rate * dt * 4294967296.0);
+        unsigned thr = !(t > 0.0) ? 0u : (t >= 4294967295.0 ? 4294967295u : (unsigned)t);
+        if (thr != b->d.tstat_thr) {
+            b->d.tstat_thr = thr;
+            invalidate_graphs(b);
+        }
+    }
     const bool record = ckpt_every > 0;
     b->rec_valid = false;
     if (record) CKS(ckpt_setup(b, (int)(nsteps / ckpt_every)));
@@ -1125,6 +1184,7 @@ md_status md_adjoint(md_box* b, const double* lam_x_T, const double* lam_v_T, do
                      double* lam_v_0, double* dL_deps, double* dL_dsigma)
 {
     if (!b) return MD_ERR_ARG;
+    if (b->all_pairs) return fail(b, MD_ERR_ARG, "md_adjoint: not in the all-pairs form");
     if (!b->rec_valid || !b->lj_set) return fail(b, MD_ERR_STATE, "md_adjoint: no recorded forward run");
     if (!lam_x_T || !lam_v_T || !lam_x_0 || !lam_v_0) return fail(b, MD_ERR_ARG, "md_adjoint: null array");
     CKS(enter(b));
@@ -1276,6 +1336,7 @@ md_status md_pair_hist(md_box* b, int32_t nbins, double rhist, double width, dou
     if (!b || !b->lj_set || nbins < 1 || nbins > 256 || !(rhist > 0) || !(width > 0) || !(rmax > 0))
         return fail(b, MD_ERR_ARG, "md_pair_hist: bad arguments");
     if (rmax > b->rl) return fail(b, MD_ERR_ARG, "md_pair_hist: rmax beyond the list radius");
+    if (b->all_pairs) return fail(b, MD_ERR_ARG, "md_pair_hist: not in the all-pairs form (no lists)");
     CKS(enter(b));
     // the lists must hold every pair below rmax at the current positions
     if (!b->fresh_abs) CKS(full_rebuild(b));
@@ -1363,6 +1424,7 @@ md_status md_get_nlist(md_box* b, int32_t* count, int64_t* nbr, int64_t cap, dou
 {
     if (!b || !count || (nbr && cap < 1)) return MD_ERR_ARG;
     if (!b->lj_set) return fail(b, MD_ERR_ARG, "md_get_nlist: md_set_lj not called");
+    if (b->all_pairs) return fail(b, MD_ERR_ARG, "md_get_nlist: the all-pairs form has no lists");
     if (b->ntot == 0) return MD_OK;
     CKS(enter(b));
     size_t cb = sizeof(int) * (size_t)b->ntot;
@@ -1482,6 +1544,7 @@ md_status md_set_tuning(md_box* b, const int32_t t[4])
 md_status md_autotune(md_box* b, int32_t reps, int32_t t[4])
 {
     if (!b || !b->lj_set || reps < 1) return fail(b, MD_ERR_ARG, "md_autotune: md_set_lj not called");
+    if (b->all_pairs) return fail(b, MD_ERR_ARG, "md_autotune: not in the all-pairs form");
     CKS(enter(b));
     // pair-force grid: blocks per SM
     const int fcand[] = {2, 3, 4, 6, 8, 12, 16, 24, 32};

@@ -154,6 +154,13 @@ struct BoxDev {
     int* any_req;              // nonzero when some replica may need a build
     unsigned long long* nbuild;
     int* err;
+    // Andersen-like thermostat: a particle collides when word 0 of its Philox
+    // draw is below tstat_thr (0: off); the bath temperature is per replica
+    unsigned tstat_thr;
+    unsigned long long tstat_seed;
+    const double* tstat_T;
+    long long* step_ctr;       // steps since md_set_thermostat (device word)
+    int all_pairs;             // every cutoff infinite: forces over all pairs, no lists
     // per-chunk FP64 partial sums
     double* part_f;            // [chunk*2 + 0] = E_pot share, [+1] = W share
     double* part_k;            // [chunk] = E_kin share
@@ -234,6 +241,23 @@ __device__ __forceinline__ int entry_k(uint32_t e)
 __device__ __forceinline__ float entry_unit(uint32_t e, int pos)
 {
     return __uint_as_float(0x4B400000u | ((e >> pos) & 3u)) - 12582913.0f;
+}
+
+// ---- Philox4x32-10 (Salmon et al., SC'11), counter-based random numbers ----
+// Ten rounds: words 0 and 2 are multiplied by two odd constants; the high
+// halves, crossed and mixed with words 1, 3 and the key, and the low halves
+// form the next counter; the key advances by two Weyl constants per round.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const unsigned hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const unsigned hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
 }
 
 // ---- bulk asynchronous copies (TMA, non-tensor) into shared memory ----
@@ -385,7 +409,8 @@ cudaError_t launch_pair_hist_grad(const BoxDev& b, int nbins, double rhist, doub
                                   const double* coef, double* grad, Launch l);
 
 // k_integrate.cu
-cudaError_t launch_integrate(const BoxDev& b, int mode, int energy, double dt, Launch l);
+cudaError_t launch_integrate(const BoxDev& b, int mode, int energy, double dt, int sidx, Launch l);
+cudaError_t launch_step_advance(long long* ctr, long long n, cudaStream_t s);
 cudaError_t launch_upload(const BoxDev& b, const double* pos, const double* vel,
                           const int* type, int set_vel, Launch l);
 cudaError_t launch_download(const BoxDev& b, double* pos, double* vel, int* img, Launch l);

@@ -31,6 +31,7 @@ EXPORTS = ["md_set_allocator", "md_batch_create", "md_box_create", "md_box_destr
            "md_get_state", "md_set_state", "md_get_nlist", "md_get_info", "md_set_tuning",
            "md_get_tuning", "md_autotune",
            "md_set_profiling", "md_get_profile", "md_pair_hist", "md_force_noalloc",
+           "md_set_thermostat",
            "md_last_error", "md_status_string"]
 
 
@@ -96,6 +97,7 @@ def load(path: str | None = None):
         L.md_pair_hist.argtypes = [vp, i32, d, d, d, vp, vp, vp]
         L.md_force_noalloc.argtypes = [vp, vp, vp, vp]
         L.md_get_profile.argtypes = [vp, vp, vp]
+        L.md_set_thermostat.argtypes = [vp, vp, d, ctypes.c_uint64]
         L.md_last_error.argtypes = [vp]
         L.md_last_error.restype = ctypes.c_char_p
         L.md_status_string.argtypes = [i32]
@@ -217,6 +219,19 @@ class Box:
         self._check(self._lib.md_set_lj(self._h, nt, eps.ctypes.data, sigma.ctypes.data,
                                         rcut.ctypes.data, float(skin), 1 if shift else 0),
                     "md_set_lj")
+        return self
+
+    def set_thermostat(self, T_bath=None, rate=0.0, seed=0):
+        """Andersen-like collisions at `rate` per unit time with a bath at
+        T_bath (scalar or one value per replica); rate 0 switches it off."""
+        if rate and T_bath is None:
+            raise ValueError("T_bath is required with rate > 0")
+        t = None
+        if T_bath is not None:
+            t = np.ascontiguousarray(np.broadcast_to(np.asarray(T_bath, dtype=np.float64), (self.nrep,)))
+        self._check(self._lib.md_set_thermostat(self._h, t.ctypes.data if t is not None else None,
+                                                float(rate), ctypes.c_uint64(int(seed))),
+                    "md_set_thermostat")
         return self
 
     def neighbour_update(self, force=False):

@@ -370,3 +370,85 @@ def test_fire_relaxes():
     pos, it, fmax = oracle.fire(s.box, s.pos, lj, s.type, maxit=5000, ftol=1e-3)
     _, e1, _ = oracle.forces(s.box, pos, lj, s.type)
     assert fmax < 1e-3 and e1 < e0
+
+
+# ---------------------------------------------------------------------------
+# Counter-based random numbers and the Andersen-like thermostat (Sec. 4: the
+# "Boltzmann" thermostat of the all-to-all workload), and the all-pairs form.
+# ---------------------------------------------------------------------------
+def test_philox_uniform_independent_and_mixing():
+    key = (1234, 5678)
+    words = np.concatenate([oracle.philox4x32((i, 0, 0, 0), key) for i in range(16384)]).astype(np.int64)
+    # uniform top bytes: chi-square with 255 degrees of freedom (mean 255, sd 22.6)
+    counts = np.bincount(words >> 24, minlength=256)
+    chi2 = float(((counts - len(words) / 256) ** 2 / (len(words) / 256)).sum())
+    assert 185 < chi2 < 330
+    # every bit set half the time (sd 0.002)
+    bits = (words[:, None] >> np.arange(32)) & 1
+    assert np.all(np.abs(bits.mean(axis=0) - 0.5) < 0.012)
+    # avalanche: one flipped counter bit changes about half of the 128 output bits
+    rng = np.random.default_rng(0)
+    dist = []
+    for _ in range(256):
+        c = rng.integers(0, 2 ** 32, size=4, dtype=np.uint64).astype(np.uint32)
+        c2 = c.copy()
+        c2[rng.integers(0, 4)] ^= np.uint32(1 << int(rng.integers(0, 32)))
+        a, b = oracle.philox4x32(c, key), oracle.philox4x32(c2, key)
+        dist.append(sum(bin(int(x) ^ int(y)).count("1") for x, y in zip(a, b)))
+    assert 61 < np.mean(dist) < 67
+    # another key gives an unrelated stream
+    other = np.concatenate([oracle.philox4x32((i, 0, 0, 0), (1235, 5678)) for i in range(4096)])
+    assert np.mean(other == words[: 4 * 4096].astype(np.uint32)) < 1e-3
+
+
+def test_thermostat_collision_rate_and_maxwell_boltzmann():
+    from scipy import stats
+    n = 20000
+    zero = np.zeros((n, 3))
+    # rate dt = 0.1: collisions ~ Binomial(n, 0.1)
+    v, hits = oracle.thermostat(zero, 2.0, 20.0, 0.005, 99, 7)
+    assert abs(hits - 0.1 * n) < 5 * np.sqrt(n * 0.1 * 0.9)
+    moved = np.any(v != 0.0, axis=1)
+    assert moved.sum() == hits
+    # a different step draws different particles
+    v2, hits2 = oracle.thermostat(zero, 2.0, 20.0, 0.005, 99, 8)
+    assert np.any(np.any(v2 != 0.0, axis=1) != moved)
+    # rate dt >= 1: every particle is redrawn from N(0, T) per component
+    v, hits = oracle.thermostat(zero, 2.0, 1000.0, 0.005, 5, 0)
+    assert hits == n
+    g = v.ravel() / np.sqrt(2.0)
+    assert abs(g.mean()) < 5 * np.sqrt(1.0 / g.size)
+    assert abs(g.var() - 1.0) < 5 * np.sqrt(2.0 / g.size)
+    assert abs(stats.kurtosis(g, fisher=False) - 3.0) < 5 * np.sqrt(24.0 / g.size)
+    assert stats.kstest(g, "norm").pvalue > 1e-4
+
+
+def test_thermostat_reaches_the_bath_temperature():
+    # canonical ensemble: <E_kin> = 3/2 N T_bath, reported as 2 E_kin/(3N - 3)
+    s = inputs.fcc_system(5, seed=31)               # 500 particles, T 0.722
+    lj = oracle.LJ(s.eps, s.sigma, s.rcut)
+    r = oracle.run(s.box, s.pos, s.vel, lj, s.skin, s.dt, 1500, thermostat=(1.5, 10.0, 3))
+    T = r["thermo"][500:, 3].mean()
+    assert abs(T - 1.5 * s.n / (s.n - 1)) < 0.04
+
+
+def test_all_pairs_forces_and_run():
+    s = inputs.fcc_system(4, seed=17)               # 256 particles, L = 6.72
+    inf = np.full((1, 1), np.inf)
+    lj = oracle.LJ(s.eps, s.sigma, inf)
+    f, e, _ = oracle.forces_brute(s.box, s.pos, lj)
+    assert np.abs(f.sum(axis=0)).max() < 1e-10 * np.abs(f).sum()          # Newton III
+    rng = np.random.default_rng(4)
+    u = rng.normal(size=s.pos.shape)
+    h = 1e-6
+    ep = oracle.forces_brute(s.box, s.pos + h * u, lj)[1]
+    em = oracle.forces_brute(s.box, s.pos - h * u, lj)[1]
+    assert (ep - em) / (2 * h) == pytest.approx(-np.sum(f * u), rel=1e-6)  # F = -grad U
+    r = oracle.run(s.box, s.pos, s.vel, lj, s.skin, s.dt, 200)
+    assert r["builds"] == 0                                                # no lists
+    E = r["thermo"][:, 0] + r["thermo"][:, 1]
+    # NVE: the minimum-image force flips at a separation of L/2 (the energy is
+    # continuous there), so the integration error is first order in dt:
+    # bounded by 5e-4 per particle over 200 steps (1.8e-4 observed)
+    assert np.abs(E - E[0]).max() / s.n < 5e-4
+    assert np.abs(r["vel"].sum(axis=0) - s.vel.sum(axis=0)).max() < 1e-10
