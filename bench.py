@@ -339,6 +339,27 @@ def bench_temperature_sweep(ljmd, inputs, steps, temps=(0.5, 0.722, 1.0, 1.5, 2.
     return out
 
 
+def bench_all_pairs(ljmd, inputs, steps_mixed, steps_fp64):
+    """The paper's first workload (Sec. 4): untruncated LJ between all pairs,
+    velocity-Verlet and the Andersen-like thermostat; N = 2000 (fcc sites,
+    rho 0.8442), T_bath 0.722, collision rate 1 per unit time, dt 0.005."""
+    s = inputs.fcc_subset_system(2000, 0.8442, 0.722, inputs.SEEDS["lj4000"] + 9)
+    inf = np.full((1, 1), np.inf)
+    out = {"workload": "all pairs (untruncated LJ, minimum image), N = 2000, rho 0.8442, dt 0.005, "
+                       "Andersen-like thermostat T 0.722 rate 1, energies every step"}
+    for prec, k in (("mixed_ds", steps_mixed), ("fp64", steps_fp64)):
+        b = ljmd.Box(s.pos, s.box, s.vel, s.type, precision=prec)
+        b.set_lj(s.eps, s.sigma, inf, s.skin, True)
+        b.set_thermostat(0.722, 1.0, 1)
+        b.integrate(s.dt, 100)
+        ms, _ = timed_call(lambda: b.integrate(s.dt, k))
+        th = b.integrate(s.dt, 100)
+        b.close()
+        out[prec] = {"value": s.n * k / (ms / 1e3), "unit": UNIT, "steps": k, "ms_per_step": ms / k,
+                     "T_kin_last100": float(th[:, 0, 3].mean())}
+    return out
+
+
 def job_throughput(ms_local, n_local, steps, dist=None):
     """Whole-job particle-steps/s over all ranks: the particles every rank
     advanced (summed) times `steps`, over the slowest rank's time (max over
@@ -449,6 +470,8 @@ def run_gpu(args):
     binary = None if args.quick else _guarded(lambda: bench_binary(ljmd, inputs, 10 * args.steps,
                                                                      max(20, args.steps)))
     tsweep = None if args.quick else _guarded(lambda: bench_temperature_sweep(ljmd, inputs, 50 * args.steps))
+    allp = None if args.quick else _guarded(lambda: bench_all_pairs(ljmd, inputs, 20 * args.steps,
+                                                                     2 * args.steps))
 
     if rank != 0:
         if dist:
@@ -481,7 +504,7 @@ def run_gpu(args):
         "rebuilds_in_timed_region": int(info1.rebuilds - info0.rebuilds),
         "adjoint_forward_ratio": adj["ratio"] if adj else None,
         "adjoint": adj, "batched": batched, "drift_lj4000": drift, "binary256k": binary,
-        "temperature_sweep": tsweep,
+        "temperature_sweep": tsweep, "all_pairs": allp,
         "tuning": tuning,
     }
     print(json.dumps(line), flush=True)

@@ -285,15 +285,39 @@ __global__ void __launch_bounds__(LJ_F64_THREADS) k_force_f64(BoxDev b)
 
 // ---------------------------------------------------------------------------
 // All pairs (Sec. 4: the untruncated LJ interaction between all particles;
-// every cutoff infinite).  One 128-particle chunk per block pass, LJ_TPP
-// threads per particle.  The replica's offsets are staged through shared
-// memory in tiles of kAllTile and thread l of a particle takes the tile's
-// entries l, l + LJ_TPP, ...  With one cell per replica all offsets are
-// from the box centre: d = o_i - o_j - L rint((o_i - o_j) / L) is the
-// minimum image.
+// every cutoff infinite).  Work items are (chunk of 128 particles, slice of
+// the replica's particles): a block sums the chunk's forces over its slice
+// (LJ_TPP threads per particle, the slice's offsets staged through shared
+// memory in tiles) into b.ap_part, and the block that completes a chunk's
+// last slice (atomic count) adds the slices in slice order (deterministic).
+// With one cell per replica all offsets are from the box centre:
+// d = o_i - o_j - L rint((o_i - o_j) / L) is the minimum image.
 // ---------------------------------------------------------------------------
 constexpr int kAllTile = 1024;
 constexpr int kAllThreads = LJ_CHUNK * LJ_TPP;
+
+__device__ __forceinline__ void slice_range(const RepDev& R, int js, int nslice, int& j0, int& j1)
+{
+    const int len = (R.n + nslice - 1) / nslice;
+    j0 = R.p_off + min(R.n, js * len);
+    j1 = R.p_off + min(R.n, (js + 1) * len);
+}
+
+// The last block of chunk w: true in every thread of it.
+__device__ __forceinline__ bool last_slice(const BoxDev& b, int w, int* s_flag)
+{
+    __syncthreads();   // this block's partials are written
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(&b.ap_cnt[w], 1u);
+        *s_flag = prev == (unsigned)(b.ap_js - 1);
+        if (*s_flag) b.ap_cnt[w] = 0u;
+    }
+    __syncthreads();
+    const bool last = *s_flag != 0;
+    if (last) __threadfence();
+    return last;
+}
 
 template <bool MONO, bool ENERGY>
 __global__ void __launch_bounds__(kAllThreads) k_force_all_f32(BoxDev b)
@@ -302,6 +326,7 @@ __global__ void __launch_bounds__(kAllThreads) k_force_all_f32(BoxDev b)
     __shared__ float4 s_lj[LJ_MAXT * LJ_MAXT];   // c12, c6, e12, e6
     __shared__ float s_esh[LJ_MAXT * LJ_MAXT];
     __shared__ double s_red[2][32];
+    __shared__ int s_flag;
     const LJDev* lj = b.lj;
     const int nt = lj->nt;
     for (int k = threadIdx.x; k < nt * nt; k += blockDim.x) {
@@ -311,9 +336,18 @@ __global__ void __launch_bounds__(kAllThreads) k_force_all_f32(BoxDev b)
     const float4 mlj = make_float4(lj->c12[0], lj->c6[0], lj->e12[0], lj->e6[0]);
     const float mesh = lj->shift[0];
     const int grp = threadIdx.x / LJ_TPP, l4 = threadIdx.x % LJ_TPP;
-    for (int w = blockIdx.x; w < b.nchunk; w += gridDim.x) {
+    const int nitem = b.nchunk * b.ap_js;
+    for (int it = blockIdx.x; it < nitem; it += gridDim.x) {
+        const int w = it / b.ap_js, js = it % b.ap_js;
         const int4 ch = b.chunk[w];
         const RepDev& R = b.rep[ch.x];
+        if (threadIdx.x == 0 && js == 0) {
+            if (w == 0) *b.any_req = 0;         // the re-binning of this step has run
+            if (w == R.chunk_off) {             // clear the replica's triggers
+                b.disp_max[ch.x] = 0u;
+                b.rebuild_req[ch.x] = 0;
+            }
+        }
         const float Lx = (float)R.L[0], Ly = (float)R.L[1], Lz = (float)R.L[2];
         const float ix = (float)(1.0 / R.L[0]), iy = (float)(1.0 / R.L[1]), iz = (float)(1.0 / R.L[2]);
         const int p = ch.y + grp;
@@ -321,7 +355,8 @@ __global__ void __launch_bounds__(kAllThreads) k_force_all_f32(BoxDev b)
         const float4 pi = b.posq[act ? p : ch.y];
         const int tb = __float_as_int(pi.w) * nt;
         float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f, vir = 0.f;
-        const int j0 = R.p_off, j1 = R.p_off + R.n;
+        int j0, j1;
+        slice_range(R, js, b.ap_js, j0, j1);
         for (int t0 = j0; t0 < j1; t0 += kAllTile) {
             const int nj = min(kAllTile, j1 - t0);
             __syncthreads();   // the previous tile is no longer read
@@ -365,14 +400,33 @@ __global__ void __launch_bounds__(kAllThreads) k_force_all_f32(BoxDev b)
             fy += __shfl_xor_sync(0xffffffffu, fy, o);
             fz += __shfl_xor_sync(0xffffffffu, fz, o);
         }
-        if (act && l4 == 0) {
-            b.force4[p] = make_float4(fx, fy, fz, 0.f);
-            if (!isfinite(fx + fy + fz)) atomicOr(&b.err[0], LJ_ERRBIT_NONFINITE);
-        }
+        if (act && l4 == 0) b.ap_part[(size_t)js * b.np + p] = make_float4(fx, fy, fz, 0.f);
         if (ENERGY) {
             double de = 0.5 * (double)e, dw = 0.5 * (double)vir;
             block_sum2(de, dw, s_red);
             if (threadIdx.x == 0) {
+                b.ap_pe[2 * (size_t)it] = de;
+                b.ap_pe[2 * (size_t)it + 1] = dw;
+            }
+        }
+        if (last_slice(b, w, &s_flag)) {
+            for (int q = ch.y + (int)threadIdx.x; q < ch.z; q += blockDim.x) {
+                float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int k = 0; k < b.ap_js; ++k) {
+                    const float4 g = __ldcg(&b.ap_part[(size_t)k * b.np + q]);
+                    f.x += g.x;
+                    f.y += g.y;
+                    f.z += g.z;
+                }
+                b.force4[q] = f;
+                if (!isfinite(f.x + f.y + f.z)) atomicOr(&b.err[0], LJ_ERRBIT_NONFINITE);
+            }
+            if (ENERGY && threadIdx.x == 0) {
+                double de = 0.0, dw = 0.0;
+                for (int k = 0; k < b.ap_js; ++k) {
+                    de += __ldcg(&b.ap_pe[2 * ((size_t)w * b.ap_js + k)]);
+                    dw += __ldcg(&b.ap_pe[2 * ((size_t)w * b.ap_js + k) + 1]);
+                }
                 b.part_f[2 * w] = de;
                 b.part_f[2 * w + 1] = dw;
             }
@@ -380,8 +434,9 @@ __global__ void __launch_bounds__(kAllThreads) k_force_all_f32(BoxDev b)
     }
 }
 
-// All pairs in FP64 (MD_PREC_FP64), one thread per particle, FP64 offsets
-// staged through shared memory.
+// All pairs in FP64 (MD_PREC_FP64): the same work items, one thread per
+// particle, FP64 offsets staged through shared memory; partial forces in
+// b.ap_part64 (3 planes per slice).
 template <bool ENERGY>
 __global__ void __launch_bounds__(LJ_CHUNK) k_force_all_f64(BoxDev b)
 {
@@ -389,12 +444,22 @@ __global__ void __launch_bounds__(LJ_CHUNK) k_force_all_f64(BoxDev b)
     __shared__ double s_x[kT], s_y[kT], s_z[kT];
     __shared__ int s_t[kT];
     __shared__ double s_red[2][32];
+    __shared__ int s_flag;
     const LJDev* lj = b.lj;
     const int nt = lj->nt;
     const int np = b.np;
-    for (int w = blockIdx.x; w < b.nchunk; w += gridDim.x) {
+    const int nitem = b.nchunk * b.ap_js;
+    for (int it = blockIdx.x; it < nitem; it += gridDim.x) {
+        const int w = it / b.ap_js, js = it % b.ap_js;
         const int4 ch = b.chunk[w];
         const RepDev& R = b.rep[ch.x];
+        if (threadIdx.x == 0 && js == 0) {
+            if (w == 0) *b.any_req = 0;
+            if (w == R.chunk_off) {
+                b.disp_max[ch.x] = 0u;
+                b.rebuild_req[ch.x] = 0;
+            }
+        }
         const double Lx = R.L[0], Ly = R.L[1], Lz = R.L[2];
         const double ix = 1.0 / Lx, iy = 1.0 / Ly, iz = 1.0 / Lz;
         const int p = ch.y + (int)threadIdx.x;
@@ -403,7 +468,8 @@ __global__ void __launch_bounds__(LJ_CHUNK) k_force_all_f64(BoxDev b)
         const double xi = b.off[pa], yi = b.off[np + pa], zi = b.off[2 * np + pa];
         const int ti = b.type[pa];
         double fx = 0.0, fy = 0.0, fz = 0.0, e = 0.0, vir = 0.0;
-        const int j0 = R.p_off, j1 = R.p_off + R.n;
+        int j0, j1;
+        slice_range(R, js, b.ap_js, j0, j1);
         for (int t0 = j0; t0 < j1; t0 += kT) {
             const int nj = min(kT, j1 - t0);
             __syncthreads();
@@ -437,15 +503,33 @@ __global__ void __launch_bounds__(LJ_CHUNK) k_force_all_f64(BoxDev b)
             }
         }
         if (act) {
-            b.force64[p] = fx;
-            b.force64[np + p] = fy;
-            b.force64[2 * np + p] = fz;
-            if (!isfinite(fx + fy + fz)) atomicOr(&b.err[0], LJ_ERRBIT_NONFINITE);
+            double* part = b.ap_part64 + (size_t)js * 3 * np;
+            part[p] = fx;
+            part[np + p] = fy;
+            part[2 * np + p] = fz;
         }
         if (ENERGY) {
             double de = 0.5 * e, dw = 0.5 * vir;
             block_sum2(de, dw, s_red);
             if (threadIdx.x == 0) {
+                b.ap_pe[2 * (size_t)it] = de;
+                b.ap_pe[2 * (size_t)it + 1] = dw;
+            }
+        }
+        if (last_slice(b, w, &s_flag)) {
+            for (int q = ch.y + (int)threadIdx.x; q < ch.z; q += blockDim.x) {
+                double f[3] = {0.0, 0.0, 0.0};
+                for (int k = 0; k < b.ap_js; ++k)
+                    for (int c = 0; c < 3; ++c) f[c] += __ldcg(&b.ap_part64[(size_t)k * 3 * np + (size_t)c * np + q]);
+                for (int c = 0; c < 3; ++c) b.force64[(size_t)c * np + q] = f[c];
+                if (!isfinite(f[0] + f[1] + f[2])) atomicOr(&b.err[0], LJ_ERRBIT_NONFINITE);
+            }
+            if (ENERGY && threadIdx.x == 0) {
+                double de = 0.0, dw = 0.0;
+                for (int k = 0; k < b.ap_js; ++k) {
+                    de += __ldcg(&b.ap_pe[2 * ((size_t)w * b.ap_js + k)]);
+                    dw += __ldcg(&b.ap_pe[2 * ((size_t)w * b.ap_js + k) + 1]);
+                }
                 b.part_f[2 * w] = de;
                 b.part_f[2 * w + 1] = dw;
             }

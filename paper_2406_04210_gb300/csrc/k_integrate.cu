@@ -49,7 +49,7 @@ __device__ __forceinline__ bool tstat_collide(const BoxDev& b, const RepDev& R, 
 }
 
 // sidx: this launch finalizes step (*b.step_ctr + sidx) (MID and LAST modes).
-template <int ACC, bool FORCE64, int MODE, bool ENERGY>
+template <int ACC, bool FORCE64, int MODE, bool ENERGY, bool TSTAT>
 __global__ void __launch_bounds__(LJ_CHUNK) k_integrate(BoxDev b, double dt, int sidx)
 {
     __shared__ double s_red[LJ_CHUNK / 32];
@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(LJ_CHUNK) k_integrate(BoxDev b, double dt, int
             // thermostat collision after the finalize of this step
             double g[3] = {0.0, 0.0, 0.0};
             bool hit = false;
-            if (MODE != LJ_STEP_FIRST && b.tstat_thr)
+            if (TSTAT && MODE != LJ_STEP_FIRST)
                 hit = tstat_collide(b, b.rep[r], r, p, *b.step_ctr + sidx, g);
             if (ACC == 0) {
                 float ekf = 0.f;
@@ -160,7 +160,11 @@ __global__ void __launch_bounds__(LJ_CHUNK) k_integrate(BoxDev b, double dt, int
 template <int ACC, bool FORCE64>
 cudaError_t launch_integrate_t(const BoxDev& b, int mode, int energy, double dt, int sidx, Launch l)
 {
-#define LJ_INT_CASE(M, E) k_integrate<ACC, FORCE64, M, E><<<l.grid, LJ_CHUNK, 0, l.s>>>(b, dt, sidx)
+#define LJ_INT_CASE(M, E)                                                                       \
+    do {                                                                                        \
+        if (b.tstat_thr) k_integrate<ACC, FORCE64, M, E, true><<<l.grid, LJ_CHUNK, 0, l.s>>>(b, dt, sidx);  \
+        else k_integrate<ACC, FORCE64, M, E, false><<<l.grid, LJ_CHUNK, 0, l.s>>>(b, dt, sidx);            \
+    } while (0)
     if (mode == LJ_STEP_FIRST) LJ_INT_CASE(LJ_STEP_FIRST, false);
     else if (mode == LJ_STEP_MID) {
         if (energy) LJ_INT_CASE(LJ_STEP_MID, true);

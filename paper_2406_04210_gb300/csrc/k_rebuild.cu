@@ -229,9 +229,57 @@ __device__ __forceinline__ unsigned long long sort_key(const BoxDev& b, int p, d
     return ((unsigned long long)ord << 32) | (unsigned)b.uidB[p];
 }
 
+// Gather particle p (old order) into slot q of cell gc, with the cell-
+// relative offsets and their FP32 copy.
+__device__ __forceinline__ void gather_one(const BoxDev& b, int p, int q, int gc, const double* centre)
+{
+    int ty = b.typeB[p];
+    float of[3];
+    for (int c = 0; c < 3; ++c) {
+        double x = b.xabsB[c * b.np + p];
+        b.xabs[c * b.np + q] = x;
+        double o = x - centre[c];
+        if (b.prec == 0) {
+            float h, l;
+            ds_from_double(o, h, l);
+            float* ofs = reinterpret_cast<float*>(b.off);
+            ofs[c * b.np + q] = h;
+            ofs[3 * b.np + c * b.np + q] = l;
+            of[c] = h;
+        } else {
+            b.off[c * b.np + q] = o;
+            of[c] = __double2float_rn(o);
+        }
+        copy_acc(b, b.vel, b.velB, c, q, p);
+        b.img[c * b.np + q] = b.imgB[c * b.np + p];
+    }
+    b.uid[q] = b.uidB[p];
+    b.type[q] = ty;
+    b.cell[q] = gc;
+    float4 pq = make_float4(of[0], of[1], of[2], __int_as_float(ty));
+    b.posq[q] = pq;
+    b.ref[q] = pq;
+}
+
 __global__ void __launch_bounds__(256) k_sortgather(BoxDev b)
 {
     if (!box_needs_rebuild(b)) return;
+    if (b.all_pairs) {
+        // one cell holds the whole replica and no list needs an order: a
+        // particle's slot is its index inside the replica, one thread each
+        for (int w = blockIdx.x; w < b.nchunk; w += gridDim.x) {
+            const int4 ch = b.chunk[w];
+            if (!rep_needs_rebuild(b, ch.x)) continue;   // block-uniform
+            const RepDev& R = b.rep[ch.x];
+            for (int s = ch.y + (int)threadIdx.x; s < ch.z; s += blockDim.x) {
+                if (s == R.p_off) atomicAdd(&b.nbuild[ch.x], 1ull);   // a re-binning
+                const int p = b.perm[s];
+                const double centre[3] = {0.5 * R.ell[0], 0.5 * R.ell[1], 0.5 * R.ell[2]};
+                gather_one(b, p, R.p_off + (b.uidB[p] - R.u_off), R.cell_off, centre);
+            }
+        }
+        return;
+    }
     const int lane = threadIdx.x & 31;
     const int wpb = blockDim.x >> 5;
     for (int gc = blockIdx.x * wpb + (threadIdx.x >> 5); gc < b.ncell; gc += gridDim.x * wpb) {
@@ -259,35 +307,7 @@ __global__ void __launch_bounds__(256) k_sortgather(BoxDev b)
                     rank += (kt < key) ? 1 : 0;
                 }
             }
-            if (idx < n) {
-                int q = s0 + rank;
-                int ty = b.typeB[p];
-                float of[3];
-                for (int c = 0; c < 3; ++c) {
-                    double x = b.xabsB[c * b.np + p];
-                    b.xabs[c * b.np + q] = x;
-                    double o = x - centre[c];
-                    if (b.prec == 0) {
-                        float h, l;
-                        ds_from_double(o, h, l);
-                        float* ofs = reinterpret_cast<float*>(b.off);
-                        ofs[c * b.np + q] = h;
-                        ofs[3 * b.np + c * b.np + q] = l;
-                        of[c] = h;
-                    } else {
-                        b.off[c * b.np + q] = o;
-                        of[c] = __double2float_rn(o);
-                    }
-                    copy_acc(b, b.vel, b.velB, c, q, p);
-                    b.img[c * b.np + q] = b.imgB[c * b.np + p];
-                }
-                b.uid[q] = b.uidB[p];
-                b.type[q] = ty;
-                b.cell[q] = gc;
-                float4 pq = make_float4(of[0], of[1], of[2], __int_as_float(ty));
-                b.posq[q] = pq;
-                b.ref[q] = pq;
-            }
+            if (idx < n) gather_one(b, p, s0 + rank, gc, centre);
         }
     }
 }

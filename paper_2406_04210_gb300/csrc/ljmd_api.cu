@@ -242,7 +242,8 @@ Launch lseg(md_box* b) { return Launch{std::max(1, std::min(b->d.nseg, b->nsm * 
 Launch lforce(md_box* b)
 {
     int per_sm = b->force_per_sm > 0 ? b->force_per_sm : (b->prec == 2 ? 12 : 6);
-    return Launch{std::max(1, std::min((int)b->d.nchunk, b->nsm * per_sm)), 0, b->stream};
+    const int items = b->all_pairs ? b->d.nchunk * std::max(1, b->d.ap_js) : b->d.nchunk;
+    return Launch{std::max(1, std::min(items, b->nsm * per_sm)), 0, b->stream};
 }
 Launch llist(md_box* b)
 {
@@ -309,7 +310,7 @@ md_status enqueue_rebuild(md_box* b, int from_abs)
     Launch lt{std::max(1, std::min((int)b->tiles.size(), b->nsm * 2)), 1024, b->stream};
     CK(b, launch_scan_tiles(b->d, b->d_tiles, (int)b->tiles.size(), b->d_tile_sum, lt));
     CK(b, launch_scatter(b->d, l));
-    CK(b, launch_sortgather(b->d, lcell(b)));
+    CK(b, launch_sortgather(b->d, b->all_pairs ? lch(b) : lcell(b)));
     if (b->all_pairs) {
         b->launches += 5;   // all pairs: binning only re-wraps and re-centres
         return MD_OK;
@@ -901,6 +902,19 @@ md_status md_set_lj(md_box* b, int32_t ntypes, const double* eps, const double* 
     bool grid_changes = !b->lj_set || rl != b->rl || all_pairs != b->all_pairs;
     b->all_pairs = all_pairs;
     b->d.all_pairs = all_pairs ? 1 : 0;
+    if (all_pairs && !b->d.ap_cnt) {
+        // j slices per chunk: enough work items to fill the GPU, each slice
+        // at least ~128 particles
+        int nmax = 1;
+        for (auto& R : b->reps) nmax = std::max(nmax, R.n);
+        const int nch = std::max(1, (int)b->chunks.size());
+        const int js = std::max(1, std::min((b->nsm * 4 + nch - 1) / nch, std::max(1, nmax / 128)));
+        b->d.ap_js = js;
+        CKS(dev_alloc(b, &b->d.ap_part, (size_t)js * b->np, false));
+        if (b->prec == MD_PREC_FP64) CKS(dev_alloc(b, &b->d.ap_part64, (size_t)js * 3 * b->np, false));
+        CKS(dev_alloc(b, &b->d.ap_pe, 2 * (size_t)js * nch, false));
+        CKS(dev_alloc(b, &b->d.ap_cnt, nch));
+    }
     if (b->lj_set && grid_changes && !b->fresh_abs) {
         CK(b, launch_materialize(b->d, lch(b)));
         b->fresh_abs = true;

@@ -161,6 +161,11 @@ struct BoxDev {
     const double* tstat_T;
     long long* step_ctr;       // steps since md_set_thermostat (device word)
     int all_pairs;             // every cutoff infinite: forces over all pairs, no lists
+    int ap_js;                 // all pairs: slices of the j range per chunk
+    float4* ap_part;           // [slice][slot] partial FP32 forces
+    double* ap_part64;         // [slice][3][slot] partial FP64 forces
+    double* ap_pe;             // [chunk * ap_js + slice][2] partial E_pot, W
+    unsigned* ap_cnt;          // per chunk: slices done (the last one resets)
     // per-chunk FP64 partial sums
     double* part_f;            // [chunk*2 + 0] = E_pot share, [+1] = W share
     double* part_k;            // [chunk] = E_kin share
