@@ -68,7 +68,8 @@ __global__ void __launch_bounds__(LJ_CHUNK) k_bin(BoxDev b, int from_abs)
         int r = ch.x;
         if (!rep_needs_rebuild(b, r)) continue;
         int p = ch.y + (int)threadIdx.x;
-        if (p >= ch.z) continue;
+        const bool act = p < ch.z;   // every lane reaches the warp-wide count below
+        if (!act) p = ch.y;
         const RepDev& R = b.rep[r];
         double x[3];
         int im[3];
@@ -101,15 +102,22 @@ __global__ void __launch_bounds__(LJ_CHUNK) k_bin(BoxDev b, int from_abs)
             q[c] = qc < 0 ? 0 : (qc >= R.nc[c] ? R.nc[c] - 1 : qc);
         }
         int gc = R.cell_off + q[0] + R.nc[0] * (q[1] + R.nc[1] * q[2]);
-        for (int c = 0; c < 3; ++c) {
-            b.xabsB[c * b.np + p] = x[c];
-            b.imgB[c * b.np + p] = im[c];
-            copy_acc(b, b.velB, b.vel, c, p, p);
+        if (act)
+            for (int c = 0; c < 3; ++c) {
+                b.xabsB[c * b.np + p] = x[c];
+                b.imgB[c * b.np + p] = im[c];
+                copy_acc(b, b.velB, b.vel, c, p, p);
+            }
+        if (act) {
+            b.uidB[p] = b.uid[p];
+            b.typeB[p] = b.type[p];
+            b.cellB[p] = gc;
         }
-        b.uidB[p] = b.uid[p];
-        b.typeB[p] = b.type[p];
-        b.cellB[p] = gc;
-        atomicAdd(&b.cell_count[gc], 1);
+        // warp-aggregated count: particles arrive in cell order, so a warp's
+        // lanes share one or two cells; one atomic per distinct cell
+        const int key = act ? gc : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        if (act && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&b.cell_count[gc], __popc(peers));
     }
 }
 
@@ -206,9 +214,16 @@ __global__ void __launch_bounds__(LJ_CHUNK) k_scatter(BoxDev b)
         int4 ch = b.chunk[w];
         if (!rep_needs_rebuild(b, ch.x)) continue;
         int p = ch.y + (int)threadIdx.x;
-        if (p >= ch.z) continue;
-        int slot = atomicAdd(&b.cell_end[b.cellB[p]], 1);
-        b.perm[slot] = p;
+        const bool act = p < ch.z;
+        // warp-aggregated slot claims: one atomic per distinct cell of the
+        // warp, each lane's slot = old cursor + its rank among the peers
+        const int c = act ? b.cellB[p] : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, c);
+        const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+        int base = 0;
+        if (act && lane == leader) base = atomicAdd(&b.cell_end[c], __popc(peers));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (act) b.perm[base + __popc(peers & ((1u << lane) - 1u))] = p;
     }
 }
 
