@@ -376,9 +376,26 @@ __global__ void __launch_bounds__(LJ_LIST_THREADS, 3) k_nlist(BoxDev b)
         if (!rep_needs_rebuild(b, r)) continue;   // block-uniform
         const RepDev& R = b.rep[r];
         __syncthreads();                          // previous segment done
-        if (threadIdx.x == 0) {
-            seg_tile(b, R, sg, s_t);
-            if (w == R.seg_off) atomicAdd(&b.nbuild[r], 1ull);
+        if (threadIdx.x < 32) {
+            // warp 0: the tile's pieces, and the segment's quads per cell
+            Tile t;
+            seg_tile_warp(b, R, sg, t);
+            const int lane = threadIdx.x;
+            if (lane == 0) {
+                s_t = t;
+                if (w == R.seg_off) atomicAdd(&b.nbuild[r], 1ull);
+            }
+            const int cbase = R.cell_off + sg.y + R.nc[0] * sg.z;
+            const int nqc = lane < sg.w ? (b.cell_end[cbase + lane] - b.cell_start[cbase + lane] + 3) >> 2 : 0;
+            int incl = nqc;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            if (lane < sg.w) s_qoff[lane] = incl - nqc;
+            if (lane == sg.w - 1) s_qoff[sg.w] = incl;
+            if (lane == 0) s_next = LJ_LIST_THREADS / 32;
         }
         if (r != cur_r && threadIdx.x < 32) {
             int k = threadIdx.x;
@@ -416,17 +433,7 @@ __global__ void __launch_bounds__(LJ_LIST_THREADS, 3) k_nlist(BoxDev b)
         const float zreach = sqrtf(rcull) + 1e-3f;
         // work units: quads of particles of one cell (the quad's particles
         // share the cell, so their candidates are the same), handed out to
-        // the warps one at a time as they finish
-        if (threadIdx.x == 0) {
-            int q = 0;
-            for (int cl = 0; cl < sg.w; ++cl) {
-                s_qoff[cl] = q;
-                q += (b.cell_end[c0 + cl] - b.cell_start[c0 + cl] + 3) >> 2;
-            }
-            s_qoff[sg.w] = q;
-            s_next = LJ_LIST_THREADS / 32;
-        }
-        __syncthreads();
+        // the warps one at a time as they finish (s_qoff, s_next set above)
         const int nquad = s_qoff[sg.w];
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
         uint16_t* flat = s_flat + warp * LJ_FLAT_MAX;

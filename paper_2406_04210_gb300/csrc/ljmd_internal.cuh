@@ -380,6 +380,57 @@ __device__ __forceinline__ void seg_tile(const BoxDev& b, const RepDev& R, int4 
     t.n = b.cell_end[c0 + S - 1] - t.p0;
 }
 
+// The same tile computed by one warp (all 32 lanes call it): lane q < 18
+// loads the bounds of piece q, the bases are an exclusive prefix over the
+// pieces.  Returns the tile in every lane's t (lane 0 may store it).
+__device__ __forceinline__ void seg_tile_warp(const BoxDev& b, const RepDev& R, int4 sg, Tile& t)
+{
+    const int lane = threadIdx.x & 31;
+    const int nx = R.nc[0], ny = R.nc[1], nz = R.nc[2];
+    const int cx0 = sg.y, cy = sg.z % ny, cz = sg.z / ny, S = sg.w;
+    int beg = 0, end = 0;
+    if (lane < 18) {
+        const int rr = lane >> 1, half = lane & 1;
+        const int dy = rr % 3 - 1, dz = rr / 3 - 1;
+        const int rowc = R.cell_off + nx * (wrapi(cy + dy, ny) + ny * wrapi(cz + dz, nz));
+        int a0, a1, b0 = 0, b1 = -1;   // cell x ranges of the row's two pieces (inclusive)
+        if (S + 2 >= nx) {
+            a0 = 0;
+            a1 = nx - 1;
+        } else if (cx0 - 1 < 0) {
+            a0 = nx - 1; a1 = nx - 1; b0 = 0; b1 = cx0 + S;
+        } else if (cx0 + S >= nx) {
+            a0 = cx0 - 1; a1 = nx - 1; b0 = 0; b1 = cx0 + S - nx;
+        } else {
+            a0 = cx0 - 1; a1 = cx0 + S;
+        }
+        if (half == 0) {
+            beg = b.cell_start[rowc + a0];
+            end = b.cell_end[rowc + a1];
+        } else if (b1 >= b0) {
+            beg = b.cell_start[rowc + b0];
+            end = b.cell_end[rowc + b1];
+        }
+    }
+    const int len = end - beg;
+    int incl = len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+#pragma unroll
+    for (int q = 0; q < 18; ++q) {
+        t.beg[q] = __shfl_sync(0xffffffffu, beg, q);
+        t.end[q] = __shfl_sync(0xffffffffu, end, q);
+        t.base[q] = __shfl_sync(0xffffffffu, incl - len, q);
+    }
+    t.total = __shfl_sync(0xffffffffu, incl, 17);
+    const int c0 = R.cell_off + cx0 + nx * sg.z;
+    t.p0 = b.cell_start[c0];
+    t.n = b.cell_end[c0 + S - 1] - t.p0;
+}
+
 // ---- launchers (defined in the kernel translation units) ----
 struct Launch {
     int grid;
