@@ -44,9 +44,10 @@ __device__ __forceinline__ void block_sum2(double& a, double& c, double (*s)[32]
 
 // One pair term of the FP32 force: accumulates f d into (fx, fy, fz) and,
 // with ENERGY, the pair energy and virial; the term is masked (not branched)
-// by the cutoff test, so the threads of a particle never diverge.
+// by the cutoff test, so the threads of a particle never diverge.  Entries
+// past a row's count name the sentinel slot, whose distance fails the test.
 template <bool MONO, bool ENERGY>
-__device__ __forceinline__ void pair_f32(unsigned ent, const float4& pj, bool valid, const float4& pi, int ti,
+__device__ __forceinline__ void pair_f32(unsigned ent, const float4& pj, const float4& pi, int ti,
                                          const float3& ell, const float4* s_lj, const float* s_rc2,
                                          const float* s_esh, int nt, const float4& mlj, float mrc2,
                                          float mesh, float& fx, float& fy, float& fz, float& e, float& vir)
@@ -72,7 +73,7 @@ __device__ __forceinline__ void pair_f32(unsigned ent, const float4& pj, bool va
     const float r6i = r2i * r2i * r2i;
     // c = (48 eps sigma^12, 24 eps sigma^6, 4 eps sigma^12, 4 eps sigma^6)
     float f = r2i * r6i * fmaf(c.x, r6i, -c.y);
-    const bool in = valid && r2 < rc2;
+    const bool in = r2 < rc2;
     f = in ? f : 0.f;
     fx = fmaf(f, dx, fx);
     fy = fmaf(f, dy, fy);
@@ -85,17 +86,17 @@ __device__ __forceinline__ void pair_f32(unsigned ent, const float4& pj, bool va
 }
 
 // FP32 pair force (Sec. 4/5), one 128-particle chunk per block pass, LJ_TPP
-// (4) threads per particle.  The threads of a particle take entries s,
-// s+4, ... of its list in blocks of GB entries per thread (the block's GB
-// gathers in flight at once, the next block's entries already loading, two
-// independent pair chains at a time), gather the neighbours' FP32 offsets
-// through L1 and combine their partial forces with shuffles.  Slots past
-// the list's end gather the particle itself and are masked.  With 4 threads
-// and GB = 4 a block covers 16 entries of the particle, so lists of ~80
-// entries carry little padding; on the 4M-particle fluid this measured
-// fastest among 2/4/8 threads per particle x 2/4/8 entries per thread.
-// MONO: a single species, parameters in registers.
-constexpr int GB = 4;   // row entries per thread per block
+// (4) threads per particle.  A particle's row is read in blocks of
+// LJ_ROW_BLOCK (16) entries, the last block's entries past the count
+// replaced by the sentinel slot; thread l8 of the particle takes entries
+// 4 l8 .. 4 l8 + 3 of each block with one 16-byte load (the next block's
+// load in flight while this one is computed), gathers the four neighbours'
+// FP32 offsets through L1
+// (four gathers in flight, two independent pair chains) and the four
+// threads combine their partial forces with shuffles.  On the 4M-particle
+// fluid 4 threads per particle x 4 entries per thread measured fastest
+// among 2/4/8 x 2/4/8.  MONO: a single species, parameters in registers.
+static_assert(LJ_TPP * 4 == LJ_ROW_BLOCK, "a row block is one 16-byte load per thread of a particle");
 template <bool MONO, bool ENERGY>
 __global__ void __launch_bounds__(LJ_FORCE_THREADS, 4) k_force_f32(BoxDev b)
 {
@@ -116,6 +117,7 @@ __global__ void __launch_bounds__(LJ_FORCE_THREADS, 4) k_force_f32(BoxDev b)
     const int K = b.K;
     const int grp = threadIdx.x / LJ_TPP, l8 = threadIdx.x % LJ_TPP;
     const float4* __restrict__ posq = b.posq;
+    const unsigned sent = entry_make(13, b.np);
     int cur_r = -1;
     float3 ell = make_float3(0.f, 0.f, 0.f);
     for (int w = blockIdx.x; w < b.nchunk; w += gridDim.x) {
@@ -143,40 +145,40 @@ __global__ void __launch_bounds__(LJ_FORCE_THREADS, 4) k_force_f32(BoxDev b)
                 pi = posq[p];
                 cnt = min(b.nbr_count[p], K);
             }
+            const int nblk = (cnt + LJ_ROW_BLOCK - 1) / LJ_ROW_BLOCK;
             const int ti = __float_as_int(pi.w);
-            const uint32_t* L = b.nbr + (size_t)K * p;
-            // thread l8 takes entries l8 + LJ_TPP i; a block of GB of them is
-            // loaded at once and the next block is in flight while this one
-            // is computed
-            const unsigned self = entry_make(13, act ? p : 0);
-            unsigned cur[GB], nxt[GB];
-#pragma unroll
-            for (int i = 0; i < GB; ++i) {
-                const int s = l8 + LJ_TPP * i;
-                cur[i] = s < cnt ? __ldcs(L + s) : self;
-            }
+            const uint4* L = reinterpret_cast<const uint4*>(b.nbr + (size_t)K * p) + l8;
             float fx = 0.f, fy = 0.f, fz = 0.f, fx2 = 0.f, fy2 = 0.f, fz2 = 0.f;
-            for (int blk = 0; blk * GB * LJ_TPP < cnt; ++blk) {
-                const int nb = (blk + 1) * GB * LJ_TPP;
-#pragma unroll
-                for (int i = 0; i < GB; ++i) {
-                    const int s = nb + l8 + LJ_TPP * i;
-                    nxt[i] = s < cnt ? __ldcs(L + s) : self;
+            // four entries: four gathers in flight, two independent pair chains
+            auto block4 = [&](const uint4& q) {
+                const float4 p0 = __ldg(posq + (q.x & LJ_IDX_MASK));
+                const float4 p1 = __ldg(posq + (q.y & LJ_IDX_MASK));
+                const float4 p2 = __ldg(posq + (q.z & LJ_IDX_MASK));
+                const float4 p3 = __ldg(posq + (q.w & LJ_IDX_MASK));
+                pair_f32<MONO, ENERGY>(q.x, p0, pi, ti, ell, s_lj, s_rc2, s_esh, nt, mlj, mrc2, mesh,
+                                       fx, fy, fz, e, vir);
+                pair_f32<MONO, ENERGY>(q.y, p1, pi, ti, ell, s_lj, s_rc2, s_esh, nt, mlj, mrc2, mesh,
+                                       fx2, fy2, fz2, e, vir);
+                pair_f32<MONO, ENERGY>(q.z, p2, pi, ti, ell, s_lj, s_rc2, s_esh, nt, mlj, mrc2, mesh,
+                                       fx, fy, fz, e, vir);
+                pair_f32<MONO, ENERGY>(q.w, p3, pi, ti, ell, s_lj, s_rc2, s_esh, nt, mlj, mrc2, mesh,
+                                       fx2, fy2, fz2, e, vir);
+            };
+            if (nblk > 0) {
+                uint4 cur = __ldcs(L);
+                for (int blk = 1; blk < nblk; ++blk) {
+                    const uint4 nxt = __ldcs(L + blk * LJ_TPP);   // in flight during this block
+                    block4(cur);
+                    cur = nxt;
                 }
-                // the neighbours of the whole block: eight gathers in flight
-                float4 pj[GB];
-#pragma unroll
-                for (int i = 0; i < GB; ++i) pj[i] = __ldg(posq + (cur[i] & LJ_IDX_MASK));
-#pragma unroll
-                for (int i = 0; i < GB; i += 2) {
-                    const int s = blk * GB * LJ_TPP + l8 + LJ_TPP * i;
-                    pair_f32<MONO, ENERGY>(cur[i], pj[i], s < cnt, pi, ti, ell, s_lj, s_rc2, s_esh, nt, mlj,
-                                           mrc2, mesh, fx, fy, fz, e, vir);
-                    pair_f32<MONO, ENERGY>(cur[i + 1], pj[i + 1], s + LJ_TPP < cnt, pi, ti, ell, s_lj, s_rc2,
-                                           s_esh, nt, mlj, mrc2, mesh, fx2, fy2, fz2, e, vir);
-                }
-#pragma unroll
-                for (int i = 0; i < GB; ++i) cur[i] = nxt[i];
+                // the row's last block: entries past the count (stale or
+                // never written) name the sentinel slot
+                const int lim = cnt - ((nblk - 1) * LJ_ROW_BLOCK + 4 * l8);
+                cur.x = lim > 0 ? cur.x : sent;
+                cur.y = lim > 1 ? cur.y : sent;
+                cur.z = lim > 2 ? cur.z : sent;
+                cur.w = lim > 3 ? cur.w : sent;
+                block4(cur);
             }
             fx += fx2;
             fy += fy2;

@@ -343,6 +343,7 @@ md_status set_all_rebuild(md_box* b)
 
 md_status alloc_lists(md_box* b, int K)
 {
+    K = round_up(K, LJ_ROW_BLOCK);   // the FP32 force kernel reads rows in whole blocks
     if (b->d.nbr) dev_release(b, b->d.nbr);
     b->d.nbr = nullptr;
     b->d.K = K;
@@ -781,7 +782,9 @@ md_status md_batch_create(md_box** out, int32_t nrep, const int64_t* n, const do
         d.rep = b->d_rep;
         d.chunk = b->d_chunk;
         d.lj = b->d_lj;
-        CKS(dev_alloc(b, &d.posq, b->np));
+        CKS(dev_alloc(b, &d.posq, (size_t)b->np + 1));
+        static const float4 sentinel = {LJ_SENTINEL_OFF, LJ_SENTINEL_OFF, LJ_SENTINEL_OFF, 0.f};   // species 0
+        CK(b, cudaMemcpyAsync(d.posq + b->np, &sentinel, sizeof(float4), cudaMemcpyHostToDevice, b->stream));
         CKS(dev_alloc(b, &d.ref, b->np));
         CKS(dev_alloc(b, &d.off, np3));
         CKS(dev_alloc(b, &d.vel, np3));

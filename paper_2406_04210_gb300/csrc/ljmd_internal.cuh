@@ -47,6 +47,12 @@
 #define LJ_SEG_MAX_CELLS 16    // most cells in one segment
 #define LJ_FLAT_MAX 1024       // candidates of one cell's 27-cell neighbourhood (list build)
 #define LJ_LIST_SMEM (32 * 1024)   // bytes of a segment's list staged in smem
+#define LJ_ROW_BLOCK 16        // the FP32 force kernel reads list rows in blocks of this many entries
+// In a row's last block the FP32 force kernel replaces the entries past the
+// count by slot np, one past the last particle: posq[np] holds this offset on
+// every axis, so that the pair distance, squared, stays finite (~3e30) and
+// far beyond any cutoff.
+#define LJ_SENTINEL_OFF 1.0e15f
 
 // error word bits (err[0]); err[1] = largest list length beyond capacity;
 // err[2] = longest list of the last builds
@@ -106,7 +112,7 @@ struct LJDev {
 // Everything a kernel needs, passed by value.
 struct BoxDev {
     int nrep, np, nchunk, ncell;
-    int K;                     // list capacity (slots per particle)
+    int K;                     // list capacity (slots per particle; a multiple of LJ_ROW_BLOCK)
     int prec;                  // md_precision
     int nt;                    // species count
     float disp_thr2;           // rebuild when |displacement|^2 > this (FP32)
@@ -121,7 +127,7 @@ struct BoxDev {
     int nseg;
     const LJDev* lj;
     // particle arrays (sorted order)
-    float4* posq;
+    float4* posq;              // np + 1 entries: the last is the sentinel (LJ_SENTINEL_OFF)
     float4* ref;
     double* off;               // FP64: off[c*np + p]; DS: float hi[c*np+p], lo[3np + c*np + p]
     double* vel;               // same layout as off

@@ -213,7 +213,9 @@ def test_capacity_overflow_recovers(ljmd):
     th_ref = ref.integrate(s.dt, 200)
     b = ljmd.from_system(s, "mixed_ds")
     count, _, _ = b.nlist()
-    b.set_tuning(capacity=int((count.max() + 7) // 8 * 8))   # full rows: a later build overflows
+    # full rows (capacities are whole blocks of 16 entries; the longest list
+    # here grows from 79 to 83 entries within 40 steps): a later build overflows
+    b.set_tuning(capacity=int((count.max() + 15) // 16 * 16))
     k0 = b.info().capacity
     th = b.integrate(s.dt, 200)
     assert b.info().capacity > k0
