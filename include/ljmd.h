@@ -202,10 +202,11 @@ md_status md_pair_hist(md_box* b, int32_t nbins, double rhist, double width,
  * md_force may grow box-owned buffers on first use; this call never
  * allocates, on the device or through the allocator hook.  Its scratch (the
  * per-128-particle energy/virial partial sums and the per-replica totals) is
- * a static device array of 65,536 doubles (512 KiB) that every GPU loading
- * the library holds until the process exits; boxes needing more (2 doubles
- * per 128 particles + 4 per replica) are rejected with MD_ERR_ARG and a
- * message.  The first call on a device looks up that array's address
+ * a static device array of 524,288 doubles (4 MiB) that every GPU loading
+ * the library holds until the process exits; boxes needing more (16 doubles
+ * per 128 particles with FP32 forces, 2 in the all-FP64 and all-pairs forms,
+ * + 4 per replica; about 4.19M particles for one box) are rejected with
+ * MD_ERR_ARG and a message.  The first call on a device looks up that array's address
  * (cudaGetSymbolAddress); make that first call before any stream capture.
  * All calls share the one array and overwrite what they use, so calls whose
  * GPU work overlaps (on different streams or boxes) race.

@@ -4,11 +4,12 @@
 // time and is memory-latency sensitive -- the CUDA version there reads packed
 // float4 particle data through the texture path).
 //
-// One thread per particle i, in cell-sorted order, walks its list:
+// The threads of particle i, in cell-sorted order, walk its list:
 //   d_ij = (o_i - o_j) - shift(k)       cell-relative offsets, FP32
 //   F_i += 48 eps/r^2 [(s/r)^12 - (s/r)^6/2] d_ij      for r^2 < rc^2
-// E_pot and W are summed per particle in the kernel's real type, reduced per
-// work item in FP64 (each pair is seen twice in a full list: factor 1/2).
+// E_pot and W are summed per thread in the kernel's real type, reduced per
+// warp (FP32 list kernel) or per work item (the others) in FP64 (each pair
+// is seen twice in a full list: factor 1/2).
 #include "ljmd_internal.cuh"
 
 namespace {
@@ -103,7 +104,6 @@ __global__ void __launch_bounds__(LJ_FORCE_THREADS, 4) k_force_f32(BoxDev b)
     __shared__ float4 s_lj[LJ_MAXT * LJ_MAXT];   // c12, c6, e12, e6
     __shared__ float s_rc2[LJ_MAXT * LJ_MAXT];
     __shared__ float s_esh[LJ_MAXT * LJ_MAXT];
-    __shared__ double s_red[2][32];
     const LJDev* lj = b.lj;
     const int nt = lj->nt;
     for (int k = threadIdx.x; k < nt * nt; k += blockDim.x) {
@@ -111,6 +111,7 @@ __global__ void __launch_bounds__(LJ_FORCE_THREADS, 4) k_force_f32(BoxDev b)
         s_rc2[k] = lj->rc2[k];
         s_esh[k] = lj->shift[k];
     }
+    __syncthreads();   // the pair tables are complete (the block's only barrier)
     const float4 mlj = make_float4(lj->c12[0], lj->c6[0], lj->e12[0], lj->e6[0]);
     const float mrc2 = lj->rc2[0];
     const float mesh = lj->shift[0];
@@ -195,11 +196,15 @@ __global__ void __launch_bounds__(LJ_FORCE_THREADS, 4) k_force_f32(BoxDev b)
             }
         }
         if (ENERGY) {
+            // one (E_pot, W) share per warp and chunk, no block barrier: the
+            // warps of a block run ahead into the next chunk independently
             double de = 0.5 * (double)e, dw = 0.5 * (double)vir;
-            block_sum2(de, dw, s_red);
-            if (threadIdx.x == 0) {
-                b.part_f[2 * w] = de;
-                b.part_f[2 * w + 1] = dw;
+            de = warp_sum_d(de);
+            dw = warp_sum_d(dw);
+            if ((threadIdx.x & 31) == 0) {
+                const size_t q = (size_t)w * LJ_FORCE_WARPS + (threadIdx.x >> 5);
+                b.part_f[2 * q] = de;
+                b.part_f[2 * q + 1] = dw;
             }
         }
     }
@@ -541,7 +546,8 @@ __global__ void __launch_bounds__(LJ_CHUNK) k_force_all_f64(BoxDev b)
 
 // E_pot, E_kin, W, T per replica from the per-chunk partial sums, in a
 // fixed order (deterministic): each block sums one item (a run of up to 256
-// chunks of one replica) and stores its 3 sums; the block that completes a
+// chunks of one replica, pf_stride (E_pot, W) shares per chunk) and stores
+// its 3 sums; the block that completes a
 // replica's last item (atomic count) adds the replica's item sums in item
 // order and resets the count.
 __global__ void __launch_bounds__(256) k_thermo(BoxDev b, double* out, int with_kin)
@@ -574,11 +580,15 @@ __global__ void __launch_bounds__(256) k_thermo(BoxDev b, double* out, int with_
         const int r = t.x;
         const RepDev& R = b.rep[r];
         double e = 0.0, w = 0.0, k = 0.0;
-        for (int c = t.y + (int)threadIdx.x; c < t.z; c += blockDim.x) {
-            e += b.part_f[2 * c];
-            w += b.part_f[2 * c + 1];
-            if (with_kin) k += b.part_k[c];
+        const int pf = b.pf_stride;
+        const double2* sh = reinterpret_cast<const double2*>(b.part_f);   // (E_pot, W) shares
+        for (int c = t.y * pf + (int)threadIdx.x; c < t.z * pf; c += blockDim.x) {
+            const double2 v = sh[c];
+            e += v.x;
+            w += v.y;
         }
+        if (with_kin)
+            for (int c = t.y + (int)threadIdx.x; c < t.z; c += blockDim.x) k += b.part_k[c];
         block_sum3(e, w, k);
         if (threadIdx.x == 0) {
             b.part_t[3 * it + 0] = e;

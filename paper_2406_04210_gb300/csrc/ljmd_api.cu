@@ -814,7 +814,8 @@ md_status md_batch_create(md_box** out, int32_t nrep, const int64_t* n, const do
         CKS(dev_alloc(b, &d.nbuild, nrep));
         CKS(dev_alloc(b, &d.err, 4));
         CKS(dev_alloc(b, &d.part_k, std::max<size_t>(1, b->chunks.size())));
-        CKS(dev_alloc(b, &d.part_f, 2 * std::max<size_t>(1, b->chunks.size())));
+        CKS(dev_alloc(b, &d.part_f, 2 * LJ_FORCE_WARPS * std::max<size_t>(1, b->chunks.size())));
+        d.pf_stride = prec == MD_PREC_FP64 ? 1 : LJ_FORCE_WARPS;
         CKS(dev_alloc(b, &b->d_type_user, std::max<int64_t>(1, ntot)));
         CK(b, cudaMemcpyAsync(b->d_rep, b->reps.data(), sizeof(RepDev) * b->reps.size(),
                               cudaMemcpyHostToDevice, b->stream));
@@ -905,6 +906,8 @@ md_status md_set_lj(md_box* b, int32_t ntypes, const double* eps, const double* 
     bool grid_changes = !b->lj_set || rl != b->rl || all_pairs != b->all_pairs;
     b->all_pairs = all_pairs;
     b->d.all_pairs = all_pairs ? 1 : 0;
+    // (E_pot, W) shares per chunk: the FP32 list kernel leaves one per warp
+    b->d.pf_stride = (all_pairs || b->prec == MD_PREC_FP64) ? 1 : LJ_FORCE_WARPS;
     if (all_pairs && !b->d.ap_cnt) {
         // j slices per chunk: enough work items to fill the GPU, each slice
         // at least ~128 particles
@@ -1629,7 +1632,7 @@ md_status md_autotune(md_box* b, int32_t reps, int32_t t[4])
 // ==========================================================================
 #include <mutex>
 
-#define LJMD_NOALLOC_DOUBLES (1 << 16)   // 512 KiB of FP64 scratch, per device
+#define LJMD_NOALLOC_DOUBLES (1 << 19)   // 4 MiB of FP64 scratch, per device
 
 // One copy per device that loads this library, held until process exit.
 static __device__ __align__(256) double g_noalloc_scratch[LJMD_NOALLOC_DOUBLES];
@@ -1644,12 +1647,13 @@ extern "C" md_status md_force_noalloc(md_box* b, double* force_out, double* epot
 {
     if (!b) return MD_ERR_ARG;
     const size_t nchunk = b->chunks.size();
-    const size_t need = 2 * nchunk + 4 * (size_t)b->nrep;
+    const size_t nshare = 2 * (size_t)b->d.pf_stride * nchunk;   // (E_pot, W) shares
+    const size_t need = nshare + 4 * (size_t)b->nrep;
     if (need > (size_t)LJMD_NOALLOC_DOUBLES) {
-        char msg[200];
+        char msg[240];
         snprintf(msg, sizeof msg,
-                 "md_force_noalloc: box needs %zu scratch doubles (2 per 128 particles + 4 per replica); "
-                 "the static scratch holds %d",
+                 "md_force_noalloc: box needs %zu scratch doubles (16 per 128 particles, 2 in the all-FP64 "
+                 "and all-pairs forms, + 4 per replica); the static scratch holds %d",
                  need, LJMD_NOALLOC_DOUBLES);
         return fail(b, MD_ERR_ARG, msg);
     }
@@ -1671,8 +1675,8 @@ extern "C" md_status md_force_noalloc(md_box* b, double* force_out, double* epot
     }
     CKS(enter(b));
     BoxDev v = b->d;
-    v.part_f = scratch;                       // every chunk's pair is overwritten
-    double* th = scratch + 2 * nchunk;        // nrep x (E_pot, E_kin, W, T), overwritten
+    v.part_f = scratch;                       // every chunk's shares are overwritten
+    double* th = scratch + nshare;            // nrep x (E_pot, E_kin, W, T), overwritten
     CKS(clear_err(b));
     CK(b, launch_force(v, 1, lforce(b)));
     CK(b, launch_thermo(v, th, 0, lthermo(b)));

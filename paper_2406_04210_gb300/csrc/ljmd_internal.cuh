@@ -41,6 +41,7 @@
 #define LJ_CHUNK 128           // particles per work item (one CTA pass)
 #define LJ_SEG_THREADS 256     // threads of the segment kernels
 #define LJ_FORCE_THREADS 256   // threads of the FP32 pair-force kernel
+#define LJ_FORCE_WARPS (LJ_FORCE_THREADS / 32)   // its (E_pot, W) shares per chunk
 #define LJ_LIST_THREADS 256    // threads of the list-build kernel
 #define LJ_F64_THREADS 128     // threads of the FP64 pair kernel (one per particle)
 #define LJ_TPP 4               // threads per particle in the pair kernels
@@ -173,7 +174,8 @@ struct BoxDev {
     double* ap_pe;             // [chunk * ap_js + slice][2] partial E_pot, W
     unsigned* ap_cnt;          // per chunk: slices done (the last one resets)
     // per-chunk FP64 partial sums
-    double* part_f;            // [chunk*2 + 0] = E_pot share, [+1] = W share
+    double* part_f;            // [(chunk*pf_stride + q)*2 + 0] = E_pot share, [+1] = W share
+    int pf_stride;             // (E_pot, W) shares per chunk: one per warp of the FP32 list kernel, else 1
     double* part_k;            // [chunk] = E_kin share
     double* part_t;            // [item*3 + 0..2] = E_pot, W, E_kin of a reduction item
     unsigned* tcount;          // per replica: reduction items finished (last one resets)

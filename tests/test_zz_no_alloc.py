@@ -51,8 +51,9 @@ def test_force_noalloc_matches_md_force_twice(ljmd):
 
 
 def test_force_noalloc_rejects_boxes_beyond_its_scratch(ljmd):
-    # 16,384 one-particle replicas need 2 x 16,384 + 4 x 16,384 doubles > 65,536
-    nrep = 16384
+    # 32,768 one-particle replicas (FP32 forces: 16 doubles per 128-particle
+    # chunk) need 16 x 32,768 + 4 x 32,768 doubles > 524,288
+    nrep = 32768
     box = np.tile([10.0, 10.0, 10.0], (nrep, 1))
     pos = np.full((nrep, 3), 5.0)
     b = ljmd.Box(pos, box, n=[1] * nrep)
