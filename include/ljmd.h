@@ -204,7 +204,7 @@ md_status md_pair_hist(md_box* b, int32_t nbins, double rhist, double width,
  * per-128-particle energy/virial partial sums and the per-replica totals) is
  * a static device array of 524,288 doubles (4 MiB) that every GPU loading
  * the library holds until the process exits; boxes needing more (16 doubles
- * per 128 particles with FP32 forces, 2 in the all-FP64 and all-pairs forms,
+ * per 128 particles with FP32 forces, 8 all-FP64, 2 in the all-pairs form,
  * + 4 per replica; about 4.19M particles for one box) are rejected with
  * MD_ERR_ARG and a message.  The first call on a device looks up that array's address
  * (cudaGetSymbolAddress); make that first call before any stream capture.

@@ -76,16 +76,16 @@ __global__ void __launch_bounds__(LJ_CHUNK) k_adj_post(BoxDev b, double* lx, dou
 // (as the force kernel).  part_g[chunk * 2P + 0..P-1] gets sum lam.dF/deps,
 // [P..2P-1] sum lam.dF/dsigma per symmetric type pair (P = nt * nt slots; the
 // (a, b) and (b, a) terms both land in the slot of min/max).  MONO keeps the
-// two sums in registers (deterministic); otherwise shared-memory atomics.
+// two sums in registers and leaves one pair per warp and chunk,
+// part_g[(chunk * LJ_FORCE_WARPS + warp) * 2 + 0/1], with no block barrier
+// (deterministic); otherwise shared-memory atomics, one 2P row per chunk.
 template <bool MONO>
 __global__ void __launch_bounds__(LJ_FORCE_THREADS) k_hvp_f32(BoxDev b, const float4* __restrict__ u_slot,
                                                               float4* hu_slot, double* part_g)
 {
-    __shared__ float4 s_shift[32];
     __shared__ float4 s_c[LJ_MAXT * LJ_MAXT];     // c12, c6, a12, a6
     __shared__ float4 s_g[LJ_MAXT * LJ_MAXT];     // g12, g6, 1/eps, rc2
     __shared__ float s_acc[2 * LJ_MAXT * LJ_MAXT];
-    __shared__ double s_red[2][32];
     const LJDev* lj = b.lj;
     const int nt = lj->nt;
     const int P = nt * nt;
@@ -93,27 +93,27 @@ __global__ void __launch_bounds__(LJ_FORCE_THREADS) k_hvp_f32(BoxDev b, const fl
         s_c[k] = make_float4(lj->c12[k], lj->c6[k], lj->a12[k], lj->a6[k]);
         s_g[k] = make_float4(lj->g12[k], lj->g6[k], lj->inv_eps[k], lj->rc2[k]);
     }
+    __syncthreads();   // the pair tables are complete
     const float4 mc = make_float4(lj->c12[0], lj->c6[0], lj->a12[0], lj->a6[0]);
     const float4 mg = make_float4(lj->g12[0], lj->g6[0], lj->inv_eps[0], lj->rc2[0]);
     const int K = b.K;
     const int grp = threadIdx.x / LJ_TPP, l8 = threadIdx.x % LJ_TPP;
     const float4* __restrict__ posq = b.posq;
     int cur_r = -1;
+    float3 ell = make_float3(0.f, 0.f, 0.f);
     for (int w = blockIdx.x; w < b.nchunk; w += gridDim.x) {
         const int4 ch = b.chunk[w];
         const int r = ch.x;
-        __syncthreads();
-        if (r != cur_r && threadIdx.x < 32) {
+        if (r != cur_r) {                       // block-uniform
             const RepDev& R = b.rep[r];
-            const int k = threadIdx.x;
-            s_shift[k] = k < 27 ? make_float4((float)(k % 3 - 1) * R.ellf[0], (float)((k / 3) % 3 - 1) * R.ellf[1],
-                                              (float)(k / 9 - 1) * R.ellf[2], 0.f)
-                                : make_float4(0.f, 0.f, 0.f, 0.f);
+            ell = make_float3(R.ellf[0], R.ellf[1], R.ellf[2]);
+            cur_r = r;
         }
-        if (!MONO)
+        if (!MONO) {   // per-chunk species-pair sums in shared memory
+            __syncthreads();
             for (int k = threadIdx.x; k < 2 * P; k += blockDim.x) s_acc[k] = 0.f;
-        cur_r = r;
-        __syncthreads();
+            __syncthreads();
+        }
         float ge = 0.f, gs = 0.f;
         for (int base = ch.y; base < ch.z; base += LJ_FORCE_THREADS / LJ_TPP) {
             const int p = base + grp;
@@ -133,10 +133,10 @@ __global__ void __launch_bounds__(LJ_FORCE_THREADS) k_hvp_f32(BoxDev b, const fl
                 const int j = (int)(ent & LJ_IDX_MASK);
                 const float4 pj = __ldg(posq + j);
                 const float4 uj = __ldg(u_slot + j);
-                const float4 sh = s_shift[entry_k(ent)];
-                const float dx = (pi.x - pj.x) - sh.x;
-                const float dy = (pi.y - pj.y) - sh.y;
-                const float dz = (pi.z - pj.z) - sh.z;
+                // d = (o_i - o_j) - (dx, dy, dz) * ell, one rounding per component
+                const float dx = fmaf(-entry_unit(ent, 26), ell.x, pi.x - pj.x);
+                const float dy = fmaf(-entry_unit(ent, 28), ell.y, pi.y - pj.y);
+                const float dz = fmaf(-entry_unit(ent, 30), ell.z, pi.z - pj.z);
                 const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                 float4 c, gg;
                 int pp = 0;
@@ -183,21 +183,12 @@ __global__ void __launch_bounds__(LJ_FORCE_THREADS) k_hvp_f32(BoxDev b, const fl
             if (act && l8 == 0) hu_slot[p] = make_float4(hx, hy, hz, 0.f);
         }
         if (MONO) {
-            double de = warp_sum_d((double)ge), ds = warp_sum_d((double)gs);
-            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-            if (lane == 0) {
-                s_red[0][warp] = de;
-                s_red[1][warp] = ds;
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                de = ds = 0.0;
-                for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
-                    de += s_red[0][k];
-                    ds += s_red[1][k];
-                }
-                part_g[2 * (size_t)w] = de;
-                part_g[2 * (size_t)w + 1] = ds;
+            // one (d/deps, d/dsigma) share per warp and chunk (no block barrier)
+            const double de = warp_sum_d((double)ge), ds = warp_sum_d((double)gs);
+            if ((threadIdx.x & 31) == 0) {
+                const size_t q = (size_t)w * LJ_FORCE_WARPS + (threadIdx.x >> 5);
+                part_g[2 * q] = de;
+                part_g[2 * q + 1] = ds;
             }
         } else {
             __syncthreads();

@@ -8,8 +8,8 @@
 //   d_ij = (o_i - o_j) - shift(k)       cell-relative offsets, FP32
 //   F_i += 48 eps/r^2 [(s/r)^12 - (s/r)^6/2] d_ij      for r^2 < rc^2
 // E_pot and W are summed per thread in the kernel's real type, reduced per
-// warp (FP32 list kernel) or per work item (the others) in FP64 (each pair
-// is seen twice in a full list: factor 1/2).
+// warp (list kernels) or per work item (all pairs) in FP64 (each pair is
+// seen twice in a full list: factor 1/2).
 #include "ljmd_internal.cuh"
 
 namespace {
@@ -216,7 +216,6 @@ template <bool ENERGY>
 __global__ void __launch_bounds__(LJ_F64_THREADS) k_force_f64(BoxDev b)
 {
     __shared__ double s_sh[3][27];
-    __shared__ double s_red[2][32];
     const LJDev* lj = b.lj;
     const int nt = lj->nt;
     const int np = b.np;
@@ -280,11 +279,12 @@ __global__ void __launch_bounds__(LJ_F64_THREADS) k_force_f64(BoxDev b)
             if (!isfinite(fx + fy + fz)) atomicOr(&b.err[0], LJ_ERRBIT_NONFINITE);
         }
         if (ENERGY) {
-            double de = 0.5 * e, dw = 0.5 * vir;
-            block_sum2(de, dw, s_red);
-            if (threadIdx.x == 0) {
-                b.part_f[2 * w] = de;
-                b.part_f[2 * w + 1] = dw;
+            // one (E_pot, W) share per warp and chunk (no block barrier)
+            double de = warp_sum_d(0.5 * e), dw = warp_sum_d(0.5 * vir);
+            if ((threadIdx.x & 31) == 0) {
+                const size_t q = (size_t)w * LJ_F64_WARPS + (threadIdx.x >> 5);
+                b.part_f[2 * q] = de;
+                b.part_f[2 * q + 1] = dw;
             }
         }
     }
@@ -588,7 +588,8 @@ __global__ void __launch_bounds__(256) k_thermo(BoxDev b, double* out, int with_
             w += v.y;
         }
         if (with_kin)
-            for (int c = t.y + (int)threadIdx.x; c < t.z; c += blockDim.x) k += b.part_k[c];
+            for (int c = t.y * LJ_KIN_WARPS + (int)threadIdx.x; c < t.z * LJ_KIN_WARPS; c += blockDim.x)
+                k += b.part_k[c];
         block_sum3(e, w, k);
         if (threadIdx.x == 0) {
             b.part_t[3 * it + 0] = e;

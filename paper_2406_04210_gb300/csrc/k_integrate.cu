@@ -52,7 +52,6 @@ __device__ __forceinline__ bool tstat_collide(const BoxDev& b, const RepDev& R, 
 template <int ACC, bool FORCE64, int MODE, bool ENERGY, bool TSTAT>
 __global__ void __launch_bounds__(LJ_CHUNK) k_integrate(BoxDev b, double dt, int sidx)
 {
-    __shared__ double s_red[LJ_CHUNK / 32];
     const int np = b.np;
     const double hdt = 0.5 * dt;
     float dt_h, dt_l;
@@ -144,15 +143,9 @@ __global__ void __launch_bounds__(LJ_CHUNK) k_integrate(BoxDev b, double dt, int
             }
         }
         if (ENERGY && MODE != LJ_STEP_FIRST) {
-            double s = warp_sum_d(0.5 * ek);
-            if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = s;
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                double t = 0.0;
-                for (int k = 0; k < LJ_CHUNK / 32; ++k) t += s_red[k];
-                b.part_k[w] = t;
-            }
-            __syncthreads();
+            // one E_kin share per warp and chunk (no block barrier)
+            const double s = warp_sum_d(0.5 * ek);
+            if ((threadIdx.x & 31) == 0) b.part_k[(size_t)w * LJ_KIN_WARPS + (threadIdx.x >> 5)] = s;
         }
     }
 }

@@ -813,9 +813,9 @@ md_status md_batch_create(md_box** out, int32_t nrep, const int64_t* n, const do
         d.tstat_thr = 0u;
         CKS(dev_alloc(b, &d.nbuild, nrep));
         CKS(dev_alloc(b, &d.err, 4));
-        CKS(dev_alloc(b, &d.part_k, std::max<size_t>(1, b->chunks.size())));
+        CKS(dev_alloc(b, &d.part_k, LJ_KIN_WARPS * std::max<size_t>(1, b->chunks.size())));
         CKS(dev_alloc(b, &d.part_f, 2 * LJ_FORCE_WARPS * std::max<size_t>(1, b->chunks.size())));
-        d.pf_stride = prec == MD_PREC_FP64 ? 1 : LJ_FORCE_WARPS;
+        d.pf_stride = prec == MD_PREC_FP64 ? LJ_F64_WARPS : LJ_FORCE_WARPS;
         CKS(dev_alloc(b, &b->d_type_user, std::max<int64_t>(1, ntot)));
         CK(b, cudaMemcpyAsync(b->d_rep, b->reps.data(), sizeof(RepDev) * b->reps.size(),
                               cudaMemcpyHostToDevice, b->stream));
@@ -906,8 +906,8 @@ md_status md_set_lj(md_box* b, int32_t ntypes, const double* eps, const double* 
     bool grid_changes = !b->lj_set || rl != b->rl || all_pairs != b->all_pairs;
     b->all_pairs = all_pairs;
     b->d.all_pairs = all_pairs ? 1 : 0;
-    // (E_pot, W) shares per chunk: the FP32 list kernel leaves one per warp
-    b->d.pf_stride = (all_pairs || b->prec == MD_PREC_FP64) ? 1 : LJ_FORCE_WARPS;
+    // (E_pot, W) shares per chunk: the list kernels leave one per warp
+    b->d.pf_stride = all_pairs ? 1 : b->prec == MD_PREC_FP64 ? LJ_F64_WARPS : LJ_FORCE_WARPS;
     if (all_pairs && !b->d.ap_cnt) {
         // j slices per chunk: enough work items to fill the GPU, each slice
         // at least ~128 particles
@@ -1244,7 +1244,8 @@ md_status md_adjoint(md_box* b, const double* lam_x_T, const double* lam_v_T, do
     CKS(snapshot(b, false));
     Launch l = lch(b);
     Launch lf = lforce(b);
-    const int nchunk = (int)b->chunks.size();
+    // parameter-gradient rows: one per chunk, one per warp and chunk for one species
+    const int nchunk = (int)b->chunks.size() * (P == 1 ? LJ_FORCE_WARPS : 1);
     const int twoP = 2 * P;
     // The replay of a segment (k recorded steps keeping the tape) and its
     // reverse sweep have the same launches for every segment: each is
@@ -1652,8 +1653,8 @@ extern "C" md_status md_force_noalloc(md_box* b, double* force_out, double* epot
     if (need > (size_t)LJMD_NOALLOC_DOUBLES) {
         char msg[240];
         snprintf(msg, sizeof msg,
-                 "md_force_noalloc: box needs %zu scratch doubles (16 per 128 particles, 2 in the all-FP64 "
-                 "and all-pairs forms, + 4 per replica); the static scratch holds %d",
+                 "md_force_noalloc: box needs %zu scratch doubles (16 per 128 particles with FP32 forces, 8 "
+                 "all-FP64, 2 for all pairs, + 4 per replica); the static scratch holds %d",
                  need, LJMD_NOALLOC_DOUBLES);
         return fail(b, MD_ERR_ARG, msg);
     }

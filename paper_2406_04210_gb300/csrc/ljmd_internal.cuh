@@ -42,8 +42,10 @@
 #define LJ_SEG_THREADS 256     // threads of the segment kernels
 #define LJ_FORCE_THREADS 256   // threads of the FP32 pair-force kernel
 #define LJ_FORCE_WARPS (LJ_FORCE_THREADS / 32)   // its (E_pot, W) shares per chunk
+#define LJ_KIN_WARPS (LJ_CHUNK / 32)   // E_kin shares per chunk (one per warp of the integrator)
 #define LJ_LIST_THREADS 256    // threads of the list-build kernel
 #define LJ_F64_THREADS 128     // threads of the FP64 pair kernel (one per particle)
+#define LJ_F64_WARPS (LJ_F64_THREADS / 32)   // its (E_pot, W) shares per chunk
 #define LJ_TPP 4               // threads per particle in the pair kernels
 #define LJ_SEG_MAX_CELLS 16    // most cells in one segment
 #define LJ_FLAT_MAX 1024       // candidates of one cell's 27-cell neighbourhood (list build)
@@ -175,8 +177,8 @@ struct BoxDev {
     unsigned* ap_cnt;          // per chunk: slices done (the last one resets)
     // per-chunk FP64 partial sums
     double* part_f;            // [(chunk*pf_stride + q)*2 + 0] = E_pot share, [+1] = W share
-    int pf_stride;             // (E_pot, W) shares per chunk: one per warp of the FP32 list kernel, else 1
-    double* part_k;            // [chunk] = E_kin share
+    int pf_stride;             // (E_pot, W) shares per chunk: one per warp of the list kernels, 1 for all pairs
+    double* part_k;            // [chunk*LJ_KIN_WARPS + warp] = E_kin share
     double* part_t;            // [item*3 + 0..2] = E_pot, W, E_kin of a reduction item
     unsigned* tcount;          // per replica: reduction items finished (last one resets)
 };
