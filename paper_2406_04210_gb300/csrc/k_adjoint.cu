@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(LJ_FORCE_THREADS) k_hvp_f32(BoxDev b, const fl
                     gg = s_g[pp];
                 }
                 const bool in = r2 < gg.w;
-                const float r2i = __fdividef(1.0f, r2);
+                const float r2i = rcp_approx(r2);
                 const float r6i = r2i * r2i * r2i;
                 float f = r2i * r6i * fmaf(c.x, r6i, -c.y);
                 float A = r2i * r2i * r6i * fmaf(c.z, r6i, -c.w);

@@ -70,7 +70,7 @@ __device__ __forceinline__ void pair_f32(unsigned ent, const float4& pj, const f
         rc2 = s_rc2[pp];
         esh = ENERGY ? s_esh[pp] : 0.f;
     }
-    const float r2i = __fdividef(1.0f, r2);
+    const float r2i = rcp_approx(r2);
     const float r6i = r2i * r2i * r2i;
     // c = (48 eps sigma^12, 24 eps sigma^6, 4 eps sigma^12, 4 eps sigma^6)
     float f = r2i * r6i * fmaf(c.x, r6i, -c.y);
@@ -80,7 +80,7 @@ __device__ __forceinline__ void pair_f32(unsigned ent, const float4& pj, const f
     fy = fmaf(f, dy, fy);
     fz = fmaf(f, dz, fz);
     if (ENERGY) {
-        const float u = r6i * fmaf(c.z, r6i, -c.w) - esh;
+        const float u = fmaf(r6i, fmaf(c.z, r6i, -c.w), -esh);
         e += in ? u : 0.f;
         vir = fmaf(f, r2, vir);
     }
@@ -386,7 +386,7 @@ __global__ void __launch_bounds__(kAllThreads) k_force_all_f32(BoxDev b)
                     c = s_lj[pp];
                     esh = ENERGY ? s_esh[pp] : 0.f;
                 }
-                const float r2i = __fdividef(1.0f, r2);
+                const float r2i = rcp_approx(r2);
                 const float r6i = r2i * r2i * r2i;
                 float f = r2i * r6i * fmaf(c.x, r6i, -c.y);
                 const bool in = act && t0 + t != p;

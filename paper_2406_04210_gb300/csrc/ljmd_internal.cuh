@@ -241,6 +241,16 @@ __device__ __forceinline__ bool rep_needs_rebuild(const BoxDev& b, int r)
 
 __device__ __forceinline__ int wrapi(int x, int n) { return x < 0 ? x + n : (x >= n ? x - n : x); }
 
+// 1/x by the hardware reciprocal (PTX rcp.approx.ftz.f32: one special-function
+// instruction, relative error within 2^-23 for normal x); the pair kernels
+// pass r^2 > 0 and finite.
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // ---- list entries ----
 __host__ __device__ __forceinline__ uint32_t entry_make(int k, int j)
 {
