@@ -92,14 +92,17 @@ __device__ __forceinline__ void pair_f32(unsigned ent, const float4& pj, const f
 // replaced by the sentinel slot; thread l8 of the particle takes entries
 // 4 l8 .. 4 l8 + 3 of each block with one 16-byte load (the next block's
 // load in flight while this one is computed), gathers the four neighbours'
-// FP32 offsets through L1
-// (four gathers in flight, two independent pair chains) and the four
-// threads combine their partial forces with shuffles.  On the 4M-particle
-// fluid 4 threads per particle x 4 entries per thread measured fastest
-// among 2/4/8 x 2/4/8.  MONO: a single species, parameters in registers.
+// FP32 offsets through L1 (four gathers in flight, two independent pair
+// chains) and the four threads combine their partial forces with shuffles.
+// The kernel is bound by gather latency: resident warps matter more than
+// gathers in flight per thread.  Six blocks of 256 per SM (40 registers, no
+// spills) measured 11 % faster than four (64 registers), and eight gathers
+// in flight at three blocks 9 % slower.  On the 4M-particle fluid 4 threads
+// per particle x 4 entries per thread measured fastest among 2/4/8 x 2/4/8.
+// MONO: a single species, parameters in registers.
 static_assert(LJ_TPP * 4 == LJ_ROW_BLOCK, "a row block is one 16-byte load per thread of a particle");
 template <bool MONO, bool ENERGY>
-__global__ void __launch_bounds__(LJ_FORCE_THREADS, 4) k_force_f32(BoxDev b)
+__global__ void __launch_bounds__(LJ_FORCE_THREADS, 6) k_force_f32(BoxDev b)
 {
     __shared__ float4 s_lj[LJ_MAXT * LJ_MAXT];   // c12, c6, e12, e6
     __shared__ float s_rc2[LJ_MAXT * LJ_MAXT];
