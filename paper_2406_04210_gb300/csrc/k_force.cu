@@ -101,8 +101,8 @@ __device__ __forceinline__ void pair_f32(unsigned ent, const float4& pj, const f
 // per particle x 4 entries per thread measured fastest among 2/4/8 x 2/4/8.
 // MONO: a single species, parameters in registers.
 static_assert(LJ_TPP * 4 == LJ_ROW_BLOCK, "a row block is one 16-byte load per thread of a particle");
-template <bool MONO, bool ENERGY>
-__global__ void __launch_bounds__(LJ_FORCE_THREADS, 6) k_force_f32(BoxDev b)
+template <bool MONO, bool ENERGY, bool SINGLE>
+__global__ void __launch_bounds__(LJ_FORCE_THREADS, SINGLE ? 8 : 6) k_force_f32(BoxDev b)
 {
     __shared__ float4 s_lj[LJ_MAXT * LJ_MAXT];   // c12, c6, e12, e6
     __shared__ float s_rc2[LJ_MAXT * LJ_MAXT];
@@ -115,9 +115,9 @@ __global__ void __launch_bounds__(LJ_FORCE_THREADS, 6) k_force_f32(BoxDev b)
         s_esh[k] = lj->shift[k];
     }
     __syncthreads();   // the pair tables are complete (the block's only barrier)
-    const float4 mlj = make_float4(lj->c12[0], lj->c6[0], lj->e12[0], lj->e6[0]);
-    const float mrc2 = lj->rc2[0];
-    const float mesh = lj->shift[0];
+    const float4 mlj = b.c1;
+    const float mrc2 = b.rc2_1;
+    const float mesh = b.esh_1;
     const int K = b.K;
     const int grp = threadIdx.x / LJ_TPP, l8 = threadIdx.x % LJ_TPP;
     const float4* __restrict__ posq = b.posq;
@@ -127,7 +127,9 @@ __global__ void __launch_bounds__(LJ_FORCE_THREADS, 6) k_force_f32(BoxDev b)
     for (int w = blockIdx.x; w < b.nchunk; w += gridDim.x) {
         const int4 ch = b.chunk[w];
         const int r = ch.x;
-        if (r != cur_r) {                       // block-uniform
+        if (SINGLE) {
+            ell = b.ell1;
+        } else if (r != cur_r) {                // block-uniform
             const RepDev& R = b.rep[r];
             ell = make_float3(R.ellf[0], R.ellf[1], R.ellf[2]);
             cur_r = r;
@@ -153,7 +155,12 @@ __global__ void __launch_bounds__(LJ_FORCE_THREADS, 6) k_force_f32(BoxDev b)
             const int ti = __float_as_int(pi.w);
             const uint4* L = reinterpret_cast<const uint4*>(b.nbr + (size_t)K * p) + l8;
             float fx = 0.f, fy = 0.f, fz = 0.f, fx2 = 0.f, fy2 = 0.f, fz2 = 0.f;
-            // four entries: four gathers in flight, two independent pair chains
+            // the second pair chain: independent partial forces, or (SINGLE,
+            // registers for occupancy) the first chain itself
+            float& gx = SINGLE ? fx : fx2;
+            float& gy = SINGLE ? fy : fy2;
+            float& gz = SINGLE ? fz : fz2;
+            // four entries: four gathers in flight
             auto block4 = [&](const uint4& q) {
                 const float4 p0 = __ldg(posq + (q.x & LJ_IDX_MASK));
                 const float4 p1 = __ldg(posq + (q.y & LJ_IDX_MASK));
@@ -162,11 +169,11 @@ __global__ void __launch_bounds__(LJ_FORCE_THREADS, 6) k_force_f32(BoxDev b)
                 pair_f32<MONO, ENERGY>(q.x, p0, pi, ti, ell, s_lj, s_rc2, s_esh, nt, mlj, mrc2, mesh,
                                        fx, fy, fz, e, vir);
                 pair_f32<MONO, ENERGY>(q.y, p1, pi, ti, ell, s_lj, s_rc2, s_esh, nt, mlj, mrc2, mesh,
-                                       fx2, fy2, fz2, e, vir);
+                                       gx, gy, gz, e, vir);
                 pair_f32<MONO, ENERGY>(q.z, p2, pi, ti, ell, s_lj, s_rc2, s_esh, nt, mlj, mrc2, mesh,
                                        fx, fy, fz, e, vir);
                 pair_f32<MONO, ENERGY>(q.w, p3, pi, ti, ell, s_lj, s_rc2, s_esh, nt, mlj, mrc2, mesh,
-                                       fx2, fy2, fz2, e, vir);
+                                       gx, gy, gz, e, vir);
             };
             if (nblk > 0) {
                 uint4 cur = __ldcs(L);
@@ -184,9 +191,11 @@ __global__ void __launch_bounds__(LJ_FORCE_THREADS, 6) k_force_f32(BoxDev b)
                 cur.w = lim > 3 ? cur.w : sent;
                 block4(cur);
             }
-            fx += fx2;
-            fy += fy2;
-            fz += fz2;
+            if (!SINGLE) {
+                fx += fx2;
+                fy += fy2;
+                fz += fz2;
+            }
 #pragma unroll
             for (int o = LJ_TPP / 2; o > 0; o >>= 1) {
                 fx += __shfl_xor_sync(0xffffffffu, fx, o);
@@ -643,12 +652,15 @@ cudaError_t launch_force(const BoxDev& b, int energy, Launch l)
     if (b.prec == 2) {
         if (energy) k_force_f64<true><<<l.grid, LJ_F64_THREADS, 0, l.s>>>(b);
         else k_force_f64<false><<<l.grid, LJ_F64_THREADS, 0, l.s>>>(b);
+    } else if (b.nt == 1 && b.nrep == 1) {
+        if (energy) k_force_f32<true, true, true><<<l.grid, LJ_FORCE_THREADS, 0, l.s>>>(b);
+        else k_force_f32<true, false, true><<<l.grid, LJ_FORCE_THREADS, 0, l.s>>>(b);
     } else if (b.nt == 1) {
-        if (energy) k_force_f32<true, true><<<l.grid, LJ_FORCE_THREADS, 0, l.s>>>(b);
-        else k_force_f32<true, false><<<l.grid, LJ_FORCE_THREADS, 0, l.s>>>(b);
+        if (energy) k_force_f32<true, true, false><<<l.grid, LJ_FORCE_THREADS, 0, l.s>>>(b);
+        else k_force_f32<true, false, false><<<l.grid, LJ_FORCE_THREADS, 0, l.s>>>(b);
     } else {
-        if (energy) k_force_f32<false, true><<<l.grid, LJ_FORCE_THREADS, 0, l.s>>>(b);
-        else k_force_f32<false, false><<<l.grid, LJ_FORCE_THREADS, 0, l.s>>>(b);
+        if (energy) k_force_f32<false, true, false><<<l.grid, LJ_FORCE_THREADS, 0, l.s>>>(b);
+        else k_force_f32<false, false, false><<<l.grid, LJ_FORCE_THREADS, 0, l.s>>>(b);
     }
     return cudaGetLastError();
 }

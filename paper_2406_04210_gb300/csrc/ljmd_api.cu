@@ -960,6 +960,9 @@ md_status md_set_lj(md_box* b, int32_t ntypes, const double* eps, const double* 
     CK(b, cudaMemcpyAsync(b->d_lj, &h, sizeof h, cudaMemcpyHostToDevice, b->stream));
     b->nt = nt;
     b->d.nt = nt;
+    b->d.c1 = make_float4(h.c12[0], h.c6[0], h.e12[0], h.e6[0]);
+    b->d.rc2_1 = h.rc2[0];
+    b->d.esh_1 = h.shift[0];
     b->skin = skin;
     b->rl = rl;
     BoxDev& d = b->d;
@@ -992,6 +995,7 @@ md_status md_set_lj(md_box* b, int32_t ntypes, const double* eps, const double* 
             maxdens = std::max(maxdens, R.n / (R.L[0] * R.L[1] * R.L[2]));
         }
         d.ncell = cell_off;
+        d.ell1 = make_float3(b->reps[0].ellf[0], b->reps[0].ellf[1], b->reps[0].ellf[2]);
         CK(b, cudaMemcpyAsync(b->d_rep, b->reps.data(), sizeof(RepDev) * b->reps.size(),
                               cudaMemcpyHostToDevice, b->stream));
         dev_release(b, d.cell_count);

@@ -121,6 +121,11 @@ struct BoxDev {
     float disp_thr2;           // rebuild when |displacement|^2 > this (FP32)
     float band;                // FP64 recheck band on |d|^2 around rl^2
     float rl2f;
+    // one species (nt == 1): its FP32 pair constants, read by the force
+    // kernel from the kernel parameters (no registers held for them)
+    float4 c1;                 // c12, c6, e12, e6
+    float rc2_1, esh_1;
+    float3 ell1;               // one replica (nrep == 1): its cell edge, FP32
     double rl2;
     const RepDev* rep;
     const int4* chunk;         // (rep, p_begin, p_end, chunk index)
