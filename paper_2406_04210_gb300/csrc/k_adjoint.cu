@@ -54,34 +54,20 @@ __global__ void __launch_bounds__(LJ_CHUNK) k_adj_pre(BoxDev b, double* lx, doub
     }
 }
 
-// post: g <- H u (this state);  lx <- lx - h/2 g  (when upd)
-__global__ void __launch_bounds__(LJ_CHUNK) k_adj_post(BoxDev b, double* lx, double* g, const float4* hu_slot,
-                                                       double h, int upd)
-{
-    for (int w = blockIdx.x; w < b.nchunk; w += gridDim.x) {
-        int4 ch = b.chunk[w];
-        int p = ch.y + (int)threadIdx.x;
-        if (p >= ch.z) continue;
-        size_t gu = (size_t)b.uid[p];
-        float4 q = hu_slot[p];
-        double hv[3] = {q.x, q.y, q.z};
-        for (int c = 0; c < 3; ++c) {
-            g[3 * gu + c] = hv[c];
-            if (upd) lx[3 * gu + c] = lx[3 * gu + c] - 0.5 * h * hv[c];
-        }
-    }
-}
-
 // HVP and parameter-gradient terms at one state, LJ_TPP threads per particle
-// (as the force kernel).  part_g[chunk * 2P + 0..P-1] gets sum lam.dF/deps,
-// [P..2P-1] sum lam.dF/dsigma per symmetric type pair (P = nt * nt slots; the
-// (a, b) and (b, a) terms both land in the slot of min/max).  MONO keeps the
-// two sums in registers and leaves one pair per warp and chunk,
+// (as the force kernel), with the adjoint update that follows it:
+//   g <- H u (user order, FP64);  lx <- lx - h/2 g   (when upd)
+// part_g[chunk * 2P + 0..P-1] accumulates weight * sum lam.dF/deps and
+// [P..2P-1] weight * sum lam.dF/dsigma per symmetric type pair (P = nt * nt
+// slots; the (a, b) and (b, a) terms both land in the slot of min/max) over
+// the states of the reverse sweep; one reduction at its end.  MONO keeps the
+// two sums in registers and accumulates one pair per warp and chunk,
 // part_g[(chunk * LJ_FORCE_WARPS + warp) * 2 + 0/1], with no block barrier
 // (deterministic); otherwise shared-memory atomics, one 2P row per chunk.
 template <bool MONO>
 __global__ void __launch_bounds__(LJ_FORCE_THREADS) k_hvp_f32(BoxDev b, const float4* __restrict__ u_slot,
-                                                              float4* hu_slot, double* part_g)
+                                                              double* lx, double* g, double h, int upd,
+                                                              const double* weight, double* part_g)
 {
     __shared__ float4 s_c[LJ_MAXT * LJ_MAXT];     // c12, c6, a12, a6
     __shared__ float4 s_g[LJ_MAXT * LJ_MAXT];     // g12, g6, 1/eps, rc2
@@ -180,19 +166,29 @@ __global__ void __launch_bounds__(LJ_FORCE_THREADS) k_hvp_f32(BoxDev b, const fl
                 hy += __shfl_xor_sync(0xffffffffu, hy, o);
                 hz += __shfl_xor_sync(0xffffffffu, hz, o);
             }
-            if (act && l8 == 0) hu_slot[p] = make_float4(hx, hy, hz, 0.f);
+            if (act && l8 == 0) {
+                const size_t gu = (size_t)b.uid[p];
+                const double hv[3] = {hx, hy, hz};
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    g[3 * gu + c] = hv[c];
+                    if (upd) lx[3 * gu + c] = lx[3 * gu + c] - 0.5 * h * hv[c];
+                }
+            }
         }
+        const double wgt = *weight;
         if (MONO) {
             // one (d/deps, d/dsigma) share per warp and chunk (no block barrier)
             const double de = warp_sum_d((double)ge), ds = warp_sum_d((double)gs);
             if ((threadIdx.x & 31) == 0) {
                 const size_t q = (size_t)w * LJ_FORCE_WARPS + (threadIdx.x >> 5);
-                part_g[2 * q] = de;
-                part_g[2 * q + 1] = ds;
+                part_g[2 * q] += wgt * de;
+                part_g[2 * q + 1] += wgt * ds;
             }
         } else {
             __syncthreads();
-            for (int k = threadIdx.x; k < 2 * P; k += blockDim.x) part_g[2 * (size_t)P * w + k] = s_acc[k];
+            for (int k = threadIdx.x; k < 2 * P; k += blockDim.x)
+                part_g[2 * (size_t)P * w + k] += wgt * (double)s_acc[k];
         }
     }
 }
@@ -362,17 +358,11 @@ cudaError_t launch_adj_pre(const BoxDev& b, double* lx, double* lv, const double
     return cudaGetLastError();
 }
 
-cudaError_t launch_adj_post(const BoxDev& b, double* lx, double* g, const float4* hu_slot, double h, int upd,
-                            Launch l)
+cudaError_t launch_hvp(const BoxDev& b, const float4* u_slot, double* lx, double* g, double h, int upd,
+                       const double* weight, double* part_g, Launch l)
 {
-    k_adj_post<<<l.grid, LJ_CHUNK, 0, l.s>>>(b, lx, g, hu_slot, h, upd);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_hvp(const BoxDev& b, const float4* u_slot, float4* hu_slot, double* part_g, Launch l)
-{
-    if (b.nt == 1) k_hvp_f32<true><<<l.grid, LJ_FORCE_THREADS, 0, l.s>>>(b, u_slot, hu_slot, part_g);
-    else k_hvp_f32<false><<<l.grid, LJ_FORCE_THREADS, 0, l.s>>>(b, u_slot, hu_slot, part_g);
+    if (b.nt == 1) k_hvp_f32<true><<<l.grid, LJ_FORCE_THREADS, 0, l.s>>>(b, u_slot, lx, g, h, upd, weight, part_g);
+    else k_hvp_f32<false><<<l.grid, LJ_FORCE_THREADS, 0, l.s>>>(b, u_slot, lx, g, h, upd, weight, part_g);
     return cudaGetLastError();
 }
 

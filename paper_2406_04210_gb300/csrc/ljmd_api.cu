@@ -131,7 +131,6 @@ struct md_box {
     double* d_wts = nullptr;
     double* d_partg = nullptr;
     float4* d_u = nullptr;
-    float4* d_hu = nullptr;
     char* d_tape = nullptr;
     size_t tape_step_bytes = 0;
     int tape_cap = 0;
@@ -1221,9 +1220,8 @@ md_status md_adjoint(md_box* b, const double* lam_x_T, const double* lam_v_T, do
         CKS(dev_alloc(b, &b->d_lv, n3));
         CKS(dev_alloc(b, &b->d_g, n3));
         CKS(dev_alloc(b, &b->d_u, np));
-        CKS(dev_alloc(b, &b->d_hu, np));
         CKS(dev_alloc(b, &b->d_theta, 2 * LJ_MAXT * LJ_MAXT));
-        CKS(dev_alloc(b, &b->d_wts, 2));
+        CKS(dev_alloc(b, &b->d_wts, 3));
         CKS(dev_alloc(b, &b->d_partg, 2 * (size_t)LJ_MAXT * LJ_MAXT * std::max<size_t>(1, b->chunks.size())));
     }
     size_t step_bytes = al256(np * 16) + 2 * al256(np * 4) + al256(np * (size_t)b->d.K * 4);
@@ -1234,9 +1232,13 @@ md_status md_adjoint(md_box* b, const double* lam_x_T, const double* lam_v_T, do
         b->tape_step_bytes = step_bytes;
         b->tape_cap = k + 1;
     }
-    const double wts[2] = {0.5 * h, h};
+    const double wts[3] = {0.5 * h, h, 1.0};   // state weights, then the final reduction's
     CK(b, cudaMemcpyAsync(b->d_wts, wts, sizeof wts, cudaMemcpyHostToDevice, b->stream));
     CK(b, cudaMemsetAsync(b->d_theta, 0, sizeof(double) * 2 * LJ_MAXT * LJ_MAXT, b->stream));
+    // parameter-gradient shares, accumulated over the whole reverse sweep
+    CK(b, cudaMemsetAsync(b->d_partg, 0,
+                          sizeof(double) * 2 * (size_t)LJ_MAXT * LJ_MAXT * std::max<size_t>(1, b->chunks.size()),
+                          b->stream));
     const void *ix, *iv;
     CKS(ensure_stage(b, 2 * n3 * sizeof(double)));
     CKS(input_ptr(b, lam_x_T, n3 * sizeof(double), &ix, 0));
@@ -1294,17 +1296,13 @@ md_status md_adjoint(md_box* b, const double* lam_x_T, const double* lam_v_T, do
             if (m == k) {
                 if (!last) continue;   // this state's HVP was done at m = 0 of the next segment
                 CK(b, launch_adj_pre(v, b->d_lx, b->d_lv, b->d_g, b->d_u, h, 0, l));
-                CK(b, launch_hvp(v, b->d_u, b->d_hu, b->d_partg, lf));
-                CK(b, launch_adj_post(v, b->d_lx, b->d_g, b->d_hu, h, 0, l));
-                CK(b, launch_param_reduce(b->d_partg, nchunk, twoP, b->d_wts, b->d_theta, b->stream));
+                CK(b, launch_hvp(v, b->d_u, b->d_lx, b->d_g, h, 0, b->d_wts, b->d_partg, lf));
             } else {
                 CK(b, launch_adj_pre(v, b->d_lx, b->d_lv, b->d_g, b->d_u, h, 1, l));
-                CK(b, launch_hvp(v, b->d_u, b->d_hu, b->d_partg, lf));
-                CK(b, launch_adj_post(v, b->d_lx, b->d_g, b->d_hu, h, 1, l));
-                CK(b, launch_param_reduce(b->d_partg, nchunk, twoP, b->d_wts + ((first && m == 0) ? 0 : 1),
-                                          b->d_theta, b->stream));
+                CK(b, launch_hvp(v, b->d_u, b->d_lx, b->d_g, h, 1, b->d_wts + ((first && m == 0) ? 0 : 1),
+                                 b->d_partg, lf));
             }
-            b->launches += 4;
+            b->launches += 2;
         }
         return MD_OK;
     };
@@ -1323,6 +1321,8 @@ md_status md_adjoint(md_box* b, const double* lam_x_T, const double* lam_v_T, do
         if (!graphs.g[form]) CKS(capture(form, [&]() { return reverse(c == C - 1, c == 0); }));
         CKS(launch(form));
     }
+    CK(b, launch_param_reduce(b->d_partg, nchunk, twoP, b->d_wts + 2, b->d_theta, b->stream));
+    b->launches += 1;
     // outputs
     bool dx = is_device_ptr(lam_x_0), dv = is_device_ptr(lam_v_0);
     CK(b, cudaMemcpyAsync(lam_x_0, b->d_lx, n3 * sizeof(double), dx ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,

@@ -479,9 +479,10 @@ cudaError_t launch_thermo(const BoxDev& b, double* out, int with_kin, Launch l);
 // k_adjoint.cu
 cudaError_t launch_adj_pre(const BoxDev& b, double* lx, double* lv, const double* g, float4* u_slot, double h,
                            int pre, Launch l);
-cudaError_t launch_adj_post(const BoxDev& b, double* lx, double* g, const float4* hu_slot, double h, int upd,
-                            Launch l);
-cudaError_t launch_hvp(const BoxDev& b, const float4* u_slot, float4* hu_slot, double* part_g, Launch l);
+// HVP of u at the state of b, g <- H u, lx <- lx - h/2 g (when upd), and
+// part_g += *weight * the state's parameter-gradient shares
+cudaError_t launch_hvp(const BoxDev& b, const float4* u_slot, double* lx, double* g, double h, int upd,
+                       const double* weight, double* part_g, Launch l);
 cudaError_t launch_param_reduce(const double* part_g, int nchunk, int twoP, const double* weight,
                                 double* theta_grad, cudaStream_t s);
 cudaError_t launch_pair_hist(const BoxDev& b, int nbins, double rhist, double width, double rmax, double* part_h,
