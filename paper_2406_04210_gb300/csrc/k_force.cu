@@ -557,14 +557,15 @@ __global__ void __launch_bounds__(LJ_CHUNK) k_force_all_f64(BoxDev b)
 }
 
 // E_pot, E_kin, W, T per replica from the per-chunk partial sums, in a
-// fixed order (deterministic): each block sums one item (a run of up to 256
-// chunks of one replica, pf_stride (E_pot, W) shares per chunk) and stores
-// its 3 sums; the block that completes a
-// replica's last item (atomic count) adds the replica's item sums in item
-// order and resets the count.
-__global__ void __launch_bounds__(256) k_thermo(BoxDev b, double* out, int with_kin)
+// fixed order (deterministic): each block of LJ_THERMO_THREADS sums one item
+// (a run of up to LJ_THERMO_CHUNKS chunks of one replica, pf_stride
+// (E_pot, W) shares and LJ_KIN_WARPS E_kin shares per chunk).  A replica
+// of one item is written out by its block directly; otherwise each block
+// stores its 3 sums and the block that completes the replica's last item
+// (atomic count) adds the item sums in item order and resets the count.
+__global__ void __launch_bounds__(LJ_THERMO_THREADS) k_thermo(BoxDev b, double* out, int with_kin)
 {
-    __shared__ double s_red[3][256 / 32];
+    __shared__ double s_red[3][LJ_THERMO_THREADS / 32];
     __shared__ int s_last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     auto block_sum3 = [&](double& e, double& w, double& k) {
@@ -577,15 +578,22 @@ __global__ void __launch_bounds__(256) k_thermo(BoxDev b, double* out, int with_
             s_red[2][warp] = k;
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            e = w = k = 0.0;
-            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
-                e += s_red[0][q];
-                w += s_red[1][q];
-                k += s_red[2][q];
-            }
+        if (warp == 0) {   // the warp sums in a fixed order: lane q holds warp q's sums
+            const int nw = blockDim.x >> 5;
+            e = lane < nw ? s_red[0][lane] : 0.0;
+            w = lane < nw ? s_red[1][lane] : 0.0;
+            k = lane < nw ? s_red[2][lane] : 0.0;
+            e = warp_sum_d(e);
+            w = warp_sum_d(w);
+            k = warp_sum_d(k);
         }
         __syncthreads();
+    };
+    auto write_out = [&](const RepDev& R, int r, double e, double w, double k) {
+        out[4 * r + 0] = e;
+        out[4 * r + 1] = k;
+        out[4 * r + 2] = w;
+        out[4 * r + 3] = R.n > 1 ? 2.0 * k / (3.0 * (double)R.n - 3.0) : 0.0;
     };
     for (int it = blockIdx.x; it < b.ntitem; it += gridDim.x) {
         const int4 t = b.titem[it];
@@ -594,15 +602,37 @@ __global__ void __launch_bounds__(256) k_thermo(BoxDev b, double* out, int with_
         double e = 0.0, w = 0.0, k = 0.0;
         const int pf = b.pf_stride;
         const double2* sh = reinterpret_cast<const double2*>(b.part_f);   // (E_pot, W) shares
-        for (int c = t.y * pf + (int)threadIdx.x; c < t.z * pf; c += blockDim.x) {
-            const double2 v = sh[c];
-            e += v.x;
-            w += v.y;
+        // four independent loads in flight per thread, then their sums
+        const int nt4 = 4 * (int)blockDim.x;
+        for (int c0 = t.y * pf; c0 < t.z * pf; c0 += nt4) {
+            double2 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int c = c0 + u * (int)blockDim.x + (int)threadIdx.x;
+                v[u] = c < t.z * pf ? sh[c] : make_double2(0.0, 0.0);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                e += v[u].x;
+                w += v[u].y;
+            }
         }
         if (with_kin)
-            for (int c = t.y * LJ_KIN_WARPS + (int)threadIdx.x; c < t.z * LJ_KIN_WARPS; c += blockDim.x)
-                k += b.part_k[c];
+            for (int c0 = t.y * LJ_KIN_WARPS; c0 < t.z * LJ_KIN_WARPS; c0 += nt4) {
+                double v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int c = c0 + u * (int)blockDim.x + (int)threadIdx.x;
+                    v[u] = c < t.z * LJ_KIN_WARPS ? b.part_k[c] : 0.0;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) k += v[u];
+            }
         block_sum3(e, w, k);
+        if (R.nti == 1) {   // block-uniform: the replica's only item
+            if (threadIdx.x == 0) write_out(R, r, e, w, k);
+            continue;
+        }
         if (threadIdx.x == 0) {
             b.part_t[3 * it + 0] = e;
             b.part_t[3 * it + 1] = w;
@@ -621,10 +651,7 @@ __global__ void __launch_bounds__(256) k_thermo(BoxDev b, double* out, int with_
             }
             block_sum3(e, w, k);
             if (threadIdx.x == 0) {
-                out[4 * r + 0] = e;
-                out[4 * r + 1] = k;
-                out[4 * r + 2] = w;
-                out[4 * r + 3] = R.n > 1 ? 2.0 * k / (3.0 * (double)R.n - 3.0) : 0.0;
+                write_out(R, r, e, w, k);
                 b.tcount[r] = 0u;
             }
         }
@@ -667,6 +694,6 @@ cudaError_t launch_force(const BoxDev& b, int energy, Launch l)
 
 cudaError_t launch_thermo(const BoxDev& b, double* out, int with_kin, Launch l)
 {
-    k_thermo<<<l.grid, 256, 0, l.s>>>(b, out, with_kin);
+    k_thermo<<<l.grid, LJ_THERMO_THREADS, 0, l.s>>>(b, out, with_kin);
     return cudaGetLastError();
 }

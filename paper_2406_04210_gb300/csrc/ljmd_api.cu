@@ -235,7 +235,7 @@ void invalidate_graphs(md_box* b)
 }
 
 Launch lch(md_box* b) { return Launch{std::max(1, std::min((int)b->d.nchunk, b->nsm * 12)), LJ_CHUNK, b->stream}; }
-Launch lthermo(md_box* b) { return Launch{std::max(1, std::min(b->d.ntitem, b->nsm * 8)), 256, b->stream}; }
+Launch lthermo(md_box* b) { return Launch{std::max(1, std::min(b->d.ntitem, b->nsm * 8)), LJ_THERMO_THREADS, b->stream}; }
 Launch lcell(md_box* b) { return Launch{std::max(1, std::min((b->d.ncell + 7) / 8, b->nsm * 8)), 256, b->stream}; }
 Launch lseg(md_box* b) { return Launch{std::max(1, std::min(b->d.nseg, b->nsm * 8)), LJ_SEG_THREADS, b->stream}; }
 Launch lforce(md_box* b)
@@ -754,8 +754,9 @@ md_status md_batch_create(md_box** out, int32_t nrep, const int64_t* n, const do
                                           (int)b->chunks.size()));
         R.nchunk = (int)b->chunks.size() - R.chunk_off;
         R.ti_off = (int)b->titems.size();
-        for (int c = 0; c < std::max(1, R.nchunk); c += 256)
-            b->titems.push_back(make_int4(r, R.chunk_off + c, R.chunk_off + std::min(c + 256, R.nchunk), 0));
+        for (int c = 0; c < std::max(1, R.nchunk); c += LJ_THERMO_CHUNKS)
+            b->titems.push_back(
+                make_int4(r, R.chunk_off + c, R.chunk_off + std::min(c + LJ_THERMO_CHUNKS, R.nchunk), 0));
         R.nti = (int)b->titems.size() - R.ti_off;
         b->reps.push_back(R);
         poff += round_up(n[r], 32);

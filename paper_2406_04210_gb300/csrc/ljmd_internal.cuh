@@ -43,6 +43,8 @@
 #define LJ_FORCE_THREADS 256   // threads of the FP32 pair-force kernel
 #define LJ_FORCE_WARPS (LJ_FORCE_THREADS / 32)   // its (E_pot, W) shares per chunk
 #define LJ_KIN_WARPS (LJ_CHUNK / 32)   // E_kin shares per chunk (one per warp of the integrator)
+#define LJ_THERMO_THREADS 256  // threads of the energy reduction
+#define LJ_THERMO_CHUNKS 256   // chunks of one energy-reduction item
 #define LJ_LIST_THREADS 256    // threads of the list-build kernel
 #define LJ_F64_THREADS 128     // threads of the FP64 pair kernel (one per particle)
 #define LJ_F64_WARPS (LJ_F64_THREADS / 32)   // its (E_pot, W) shares per chunk
