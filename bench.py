@@ -517,7 +517,7 @@ def run_gpu(args):
 #: variant), from the ncu capture summarised in profiles/k_force_f32_lj256k.md
 #: (256,000 particles, scaled by the particle count); None when the kernel has
 #: changed since.
-DRAM_BYTES_PER_PARTICLE = 417.5
+DRAM_BYTES_PER_PARTICLE = 416.8
 
 
 def main():
