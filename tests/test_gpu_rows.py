@@ -32,9 +32,10 @@ def _scale(box, pos, rc):
     d -= box * np.rint(d / box)
     r2 = np.einsum("ijk,ijk->ij", d, d)
     np.fill_diagonal(r2, np.inf)
-    r2 = np.where(r2 < rc * rc, r2, np.inf)
+    near = r2 < rc * rc
+    r2 = np.where(near, r2, 1.0)              # pairs beyond rc (and i = j) contribute 0
     s6 = r2 ** -3
-    f = 48.0 / r2 * (s6 * s6 - 0.5 * s6)
+    f = np.where(near, 48.0 / r2 * (s6 * s6 - 0.5 * s6), 0.0)
     return np.maximum((np.abs(f) * np.sqrt(r2)).sum(axis=1), 1.0)
 
 
