@@ -233,8 +233,10 @@ __global__ void __launch_bounds__(LJ_CHUNK) k_scatter(BoxDev b)
 // user index (count of smaller keys; keys are unique), so the layout is a
 // deterministic function of the positions and the list build can take, in
 // every neighbour cell, the contiguous run of candidates within reach along
-// z.  Gather the state into the sorted arrays and derive the cell-relative
-// offsets and their FP32 copy.
+// z.  The ranks are written as each member's final slot (dst); k_gather then
+// moves the state into the sorted arrays, one thread per particle, and
+// derives the cell-relative offsets and their FP32 copy.  (All pairs: one
+// cell per replica, no order; k_sortgather gathers directly.)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ unsigned long long sort_key(const BoxDev& b, int p, double zc)
 {
@@ -322,8 +324,27 @@ __global__ void __launch_bounds__(256) k_sortgather(BoxDev b)
                     rank += (kt < key) ? 1 : 0;
                 }
             }
-            if (idx < n) gather_one(b, p, s0 + rank, gc, centre);
+            if (idx < n) b.dst[s0 + idx] = s0 + rank;
         }
+    }
+}
+
+__global__ void __launch_bounds__(LJ_CHUNK) k_gather(BoxDev b)
+{
+    if (b.all_pairs || !box_needs_rebuild(b)) return;
+    for (int w = blockIdx.x; w < b.nchunk; w += gridDim.x) {
+        const int4 ch = b.chunk[w];
+        if (!rep_needs_rebuild(b, ch.x)) continue;   // block-uniform
+        const int s = ch.y + (int)threadIdx.x;
+        if (s >= ch.z) continue;
+        const RepDev& R = b.rep[ch.x];
+        const int p = b.perm[s];
+        const int gc = b.cellB[p];
+        int cx, cy;
+        const int cz = cell_coords(R, gc, cx, cy);
+        const double centre[3] = {((double)cx + 0.5) * R.ell[0], ((double)cy + 0.5) * R.ell[1],
+                                  ((double)cz + 0.5) * R.ell[2]};
+        gather_one(b, p, b.dst[s], gc, centre);
     }
 }
 
@@ -644,9 +665,12 @@ cudaError_t launch_scatter(const BoxDev& b, Launch l)
     return cudaGetLastError();
 }
 
-cudaError_t launch_sortgather(const BoxDev& b, Launch l)
+cudaError_t launch_sortgather(const BoxDev& b, Launch l, Launch lg)
 {
     k_sortgather<<<l.grid, 256, 0, l.s>>>(b);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || b.all_pairs) return e;
+    k_gather<<<lg.grid, LJ_CHUNK, 0, lg.s>>>(b);
     return cudaGetLastError();
 }
 

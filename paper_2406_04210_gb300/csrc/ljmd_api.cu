@@ -309,13 +309,13 @@ md_status enqueue_rebuild(md_box* b, int from_abs)
     Launch lt{std::max(1, std::min((int)b->tiles.size(), b->nsm * 2)), 1024, b->stream};
     CK(b, launch_scan_tiles(b->d, b->d_tiles, (int)b->tiles.size(), b->d_tile_sum, lt));
     CK(b, launch_scatter(b->d, l));
-    CK(b, launch_sortgather(b->d, b->all_pairs ? lch(b) : lcell(b)));
+    CK(b, launch_sortgather(b->d, b->all_pairs ? lch(b) : lcell(b), lch(b)));
     if (b->all_pairs) {
         b->launches += 5;   // all pairs: binning only re-wraps and re-centres
         return MD_OK;
     }
     CK(b, launch_nlist(b->d, llist(b)));
-    b->launches += 6;
+    b->launches += 7;   // bin, scan x2, scatter, rank, gather, list
     return MD_OK;
 }
 
@@ -802,6 +802,7 @@ md_status md_batch_create(md_box** out, int32_t nrep, const int64_t* n, const do
         CKS(dev_alloc(b, &d.typeB, b->np));
         CKS(dev_alloc(b, &d.cellB, b->np));
         CKS(dev_alloc(b, &d.perm, b->np));
+        CKS(dev_alloc(b, &d.dst, b->np));
         CKS(dev_alloc(b, &d.nbr_count, b->np));
         CKS(dev_alloc(b, &d.disp_max, nrep));
         CKS(dev_alloc(b, &d.rebuild_req, nrep));

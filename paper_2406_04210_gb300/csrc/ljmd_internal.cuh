@@ -156,6 +156,7 @@ struct BoxDev {
     int* typeB;
     int* cellB;
     int* perm;                 // slot -> old index, during a rebuild
+    int* dst;                  // slot of perm -> final slot (ranked in its cell), during a rebuild
     // cells
     int* cell_count;
     int* cell_start;
@@ -471,7 +472,7 @@ cudaError_t launch_scan_tiles(const BoxDev& b, const int4* tiles, int ntiles, in
                               Launch l);
 int ljmd_scan_tile_cells();
 cudaError_t launch_scatter(const BoxDev& b, Launch l);
-cudaError_t launch_sortgather(const BoxDev& b, Launch l);
+cudaError_t launch_sortgather(const BoxDev& b, Launch l, Launch lg);   // rank (l), then gather (lg) unless all pairs
 cudaError_t launch_nlist(const BoxDev& b, Launch l);
 
 // k_force.cu
