@@ -256,7 +256,8 @@ md_status md_get_info(md_box* b, md_info* out);
  *   t[2] cells per list-build segment, <= 16      (0 = automatic: ~1400
  *        particles per 27-cell tile)
  *   t[3] neighbour-list slots per particle       (0 = automatic: fitted to
- *        1.1 x the longest list + 8 after the first build)
+ *        1.1 x the longest list + 8 after the first build); always rounded
+ *        up to a multiple of 16 (the FP32 force kernel reads 16-entry blocks)
  * Lists always regrow by themselves when a build needs more slots.
  * md_set_tuning applies t now (rebuilding the lists if t[2] or t[3] asks);
  * md_get_tuning reads the current values. */

@@ -21,8 +21,10 @@
 //     d_ij = (o_i - o_j) - (dx, dy, dz) * cell edge, decoded with integer and
 //     FP32 arithmetic (no table).  The stencil code k = 9(dz+1) + 3(dy+1) +
 //     (dx+1) orders the 27 cells.
-//     Entry s of particle p is nbr[p K + s] (K a multiple of 8): the 4 threads
-//     of a particle read 4 consecutive entries at a time.
+//     Entry s of particle p is nbr[p K + s] (K a multiple of 16): the FP32
+//     force kernel reads a row in blocks of 16 entries, one 16-byte load per
+//     thread of the particle; entries past the count are never written, and
+//     the kernel replaces them by the sentinel slot np in the last block.
 //   * the list build works per segment with the tile staged in shared memory;
 //     the pair-force kernels work per 128-particle chunk, 4 threads per
 //     particle, and gather neighbour offsets through L1 (the 64 particles of a
