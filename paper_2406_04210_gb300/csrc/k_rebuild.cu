@@ -342,8 +342,10 @@ __global__ void __launch_bounds__(LJ_CHUNK) k_gather(BoxDev b)
         const int gc = b.cellB[p];
         int cx, cy;
         const int cz = cell_coords(R, gc, cx, cy);
-        const double centre[3] = {((double)cx + 0.5) * R.ell[0], ((double)cy + 0.5) * R.ell[1],
-                                  ((double)cz + 0.5) * R.ell[2]};
+        // the centre rounded on its own (no FMA with the offset's subtraction),
+        // as the ranking kernel computes it
+        const double centre[3] = {__dmul_rn((double)cx + 0.5, R.ell[0]), __dmul_rn((double)cy + 0.5, R.ell[1]),
+                                  __dmul_rn((double)cz + 0.5, R.ell[2])};
         gather_one(b, p, b.dst[s], gc, centre);
     }
 }
