@@ -237,7 +237,6 @@ void invalidate_graphs(md_box* b)
 Launch lch(md_box* b) { return Launch{std::max(1, std::min((int)b->d.nchunk, b->nsm * 12)), LJ_CHUNK, b->stream}; }
 Launch lthermo(md_box* b) { return Launch{std::max(1, std::min(b->d.ntitem, b->nsm * 8)), LJ_THERMO_THREADS, b->stream}; }
 Launch lcell(md_box* b) { return Launch{std::max(1, std::min((b->d.ncell + 7) / 8, b->nsm * 8)), 256, b->stream}; }
-Launch lseg(md_box* b) { return Launch{std::max(1, std::min(b->d.nseg, b->nsm * 8)), LJ_SEG_THREADS, b->stream}; }
 Launch lforce(md_box* b)
 {
     int per_sm = b->force_per_sm > 0 ? b->force_per_sm : (b->prec == 2 ? 12 : 6);

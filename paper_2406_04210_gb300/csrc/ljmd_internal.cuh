@@ -41,7 +41,6 @@
 #define LJ_TILE_MAX (1 << LJ_TILE_BITS)
 #define LJ_TILE_MASK (LJ_TILE_MAX - 1)
 #define LJ_CHUNK 128           // particles per work item (one CTA pass)
-#define LJ_SEG_THREADS 256     // threads of the segment kernels
 #define LJ_FORCE_THREADS 256   // threads of the FP32 pair-force kernel
 #define LJ_FORCE_WARPS (LJ_FORCE_THREADS / 32)   // its (E_pot, W) shares per chunk
 #define LJ_KIN_WARPS (LJ_CHUNK / 32)   // E_kin shares per chunk (one per warp of the integrator)
