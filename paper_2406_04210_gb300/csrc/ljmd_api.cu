@@ -59,6 +59,9 @@ struct md_box {
     cudaStream_t ustream = nullptr;
     cudaStream_t stream = nullptr;
     cudaEvent_t ev = nullptr;
+    // the energy reduction's branch of the step graph (it overlaps the list update)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     md_alloc_fn alloc = nullptr;
     md_free_fn free_ = nullptr;
     void* actx = nullptr;
@@ -505,37 +508,52 @@ md_status enqueue_steps(md_box* b, int64_t n, double dt, int energy, double* rin
                         bool tape = false)
 {
     Launch l = lch(b);
-    Launch lt = lthermo(b);
+    // The energy reduction of step s reads the force shares of step s - 1 and
+    // the kinetic shares of this integrate: it runs on a branch (side stream)
+    // beside the list update and joins before the force kernel rewrites them.
+    const Launch lt{lthermo(b).grid, LJ_THERMO_THREADS, b->side};
     size_t rs = (size_t)b->nrep * 4;
-    auto mark = [&](int64_t s, int ph, int end) -> cudaError_t {
+    auto mark = [&](int64_t s, int ph, int end, cudaStream_t st) -> cudaError_t {
         if (!ge) return cudaSuccess;
         size_t k = (size_t)(s * 4 + ph);
         ge->used[k] = 1;
         // an external record becomes an event-record node of the graph
-        return cudaEventRecordWithFlags(ge->ev[2 * k + end], b->stream, cudaEventRecordExternal);
+        return cudaEventRecordWithFlags(ge->ev[2 * k + end], st, cudaEventRecordExternal);
+    };
+    bool joined = true;
+    auto join = [&]() -> cudaError_t {
+        if (joined) return cudaSuccess;
+        joined = true;
+        return cudaStreamWaitEvent(b->stream, b->ev_join, 0);
     };
     for (int64_t s = 0; s <= n; ++s) {
         int mode = s == 0 ? LJ_STEP_FIRST : (s == n ? LJ_STEP_LAST : LJ_STEP_MID);
-        CK(b, mark(s, 0, 0));
+        CK(b, mark(s, 0, 0, b->stream));
         CK(b, launch_integrate(b->d, mode, s == 0 ? 0 : energy, dt, (int)(s > 0 ? s - 1 : 0), l));
-        CK(b, mark(s, 0, 1));
+        CK(b, mark(s, 0, 1, b->stream));
         b->launches += 1;
         if (s > 0 && energy) {
-            CK(b, mark(s, 3, 0));
+            CK(b, cudaEventRecord(b->ev_fork, b->stream));
+            CK(b, cudaStreamWaitEvent(b->side, b->ev_fork, 0));
+            CK(b, mark(s, 3, 0, b->side));
             CK(b, launch_thermo(b->d, ring + (s - 1) * rs, 1, lt));
-            CK(b, mark(s, 3, 1));
+            CK(b, mark(s, 3, 1, b->side));
+            CK(b, cudaEventRecord(b->ev_join, b->side));
+            joined = false;
             b->launches += 1;
         }
         if (s == n) break;
-        CK(b, mark(s, 1, 0));
+        CK(b, mark(s, 1, 0, b->stream));
         CKS(enqueue_rebuild(b, 0));
-        CK(b, mark(s, 1, 1));
-        CK(b, mark(s, 2, 0));
+        CK(b, mark(s, 1, 1, b->stream));
+        CK(b, join());
+        CK(b, mark(s, 2, 0, b->stream));
         CK(b, launch_force(b->d, energy, lforce(b)));
-        CK(b, mark(s, 2, 1));
+        CK(b, mark(s, 2, 1, b->stream));
         b->launches += 1;
         if (tape) CKS(tape_save(b, (int)s + 1));
     }
+    CK(b, join());
     // steps since md_set_thermostat (the thermostat's counter), on the device
     if (!tape) {
         CK(b, launch_step_advance(b->d.step_ctr, n, b->stream));
@@ -731,8 +749,15 @@ md_status md_batch_create(md_box** out, int32_t nrep, const int64_t* n, const do
     cudaGetDevice(&b->device);
     cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, b->device);
     if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
+        if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+        if (b->side) cudaStreamDestroy(b->side);
+        if (b->ev) cudaEventDestroy(b->ev);
+        if (b->stream) cudaStreamDestroy(b->stream);
         delete b;
         return MD_ERR_CUDA;
     }
@@ -861,6 +886,9 @@ md_status md_box_destroy(md_box* b)
     for (auto& a : b->allocs) raw_free(b, a.p);
     b->allocs.clear();
     if (b->ev) cudaEventDestroy(b->ev);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->ev_join) cudaEventDestroy(b->ev_join);
+    if (b->side) cudaStreamDestroy(b->side);
     if (b->stream) cudaStreamDestroy(b->stream);
     delete b;
     return MD_OK;
