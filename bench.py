@@ -404,19 +404,23 @@ def run_gpu(args):
                          device="cuda")
     if args.warmup:
         box.integrate(s.dt, args.warmup, thermo=True, out=thermo[: args.warmup])
-    box.set_profiling(True)
     info0 = box.info()
     sampler = ClockSampler(_gpu_smi_id(local))
     if dist:
         dist.barrier()
     sampler.start()
-    ms = timed_integrate(box, s.dt, args.steps, thermo[: args.steps])
+    ms = timed_integrate(box, s.dt, args.steps, thermo[: args.steps])   # no phase events
     clocks = sampler.stop()
     info1 = box.info()
-    prof = box.profile()
     launches = int(info1.launches - info0.launches)
     th = thermo[: args.steps].cpu().numpy()
     value, ms = job_throughput(ms, n, args.steps, dist)
+    # phase breakdown and the force kernel's in-graph duration: the next K
+    # steps again, with CUDA events captured into the step graph
+    box.set_profiling(True)
+    box.integrate(s.dt, args.steps, thermo=True, out=thermo[: args.steps])
+    torch.cuda.synchronize()
+    prof = box.profile()
 
     # roofline of the dominant kernel (pair force), timed in the graph
     f_ms, f_n = prof["force"]
