@@ -99,7 +99,9 @@ __device__ __forceinline__ void pair_f32(unsigned ent, const float4& pj, const f
 // spills) measured 11 % faster than four (64 registers), and eight gathers
 // in flight at three blocks 9 % slower.  On the 4M-particle fluid 4 threads
 // per particle x 4 entries per thread measured fastest among 2/4/8 x 2/4/8.
-// MONO: a single species, parameters in registers.
+// MONO: a single species, its pair constants read from the kernel
+// parameters.  SINGLE (MONO and one replica): the cell edge from the
+// parameters too and one pair chain, 32 registers, eight blocks per SM.
 static_assert(LJ_TPP * 4 == LJ_ROW_BLOCK, "a row block is one 16-byte load per thread of a particle");
 template <bool MONO, bool ENERGY, bool SINGLE>
 __global__ void __launch_bounds__(LJ_FORCE_THREADS, SINGLE ? 8 : 6) k_force_f32(BoxDev b)
