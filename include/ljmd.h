@@ -246,6 +246,11 @@ typedef struct {
     double rlist;           /* max(rcut) + skin                               */
     int64_t launches;       /* kernels launched so far (graph nodes included) */
     int64_t list_entries;   /* sum of list lengths at the last builds          */
+    int64_t record_id;      /* serial number of the recorded forward run that
+                               md_adjoint would differentiate now: each
+                               md_integrate with ckpt_every > 0 takes the next
+                               number; 0 when no record is valid (any call that
+                               changes the state or the parameters drops it) */
 } md_info;
 
 md_status md_get_info(md_box* b, md_info* out);

@@ -16,8 +16,10 @@
  *     drift) and `finalize` (half kick) around the force evaluation (Sec. 3,
  *     Code structure; Fig. 1).
  * The paper prints no formulas; the textbook forms (Allen & Tildesley, cited
- * in Sec. 1 and Sec. 3) are written out here.  Readings where the paper is
- * silent are fixed in DESIGN.md ("Readings of the paper").
+ * in Sec. 1 and Sec. 3) are written out here.  Where the paper is silent the
+ * reading taken is stated beside the function that takes it (reduced units
+ * and unit mass, a strict cutoff test, a full list with skin, 3N - 3 degrees
+ * of freedom).
  *
  * Conventions: reduced LJ units, unit mass (m = 1), k_B = 1.  Arrays are
  * n x 3 row-major (AoS) FP64 in user order.  Pair parameter tables are
@@ -35,8 +37,9 @@
  *   or_hist, or_hist_grad   normalisation sum and central differences
  *   or_adjoint              central differences of a trajectory loss
  *   or_fire                 monotone descent to max|F| < ftol (input relaxation)
- *   or_philox4x32           uniformity and stream independence (chi-square),
- *                           Gaussian moments of the Box-Muller draws
+ *   or_philox4x32           the published known-answer vectors of Philox4x32-10
+ *                           (Random123), uniformity and stream independence
+ *                           (chi-square), Gaussian moments of the Box-Muller draws
  *   or_run with a thermostat  collision frequency = rate dt (binomial), canonical
  *                           <E_kin> = 3/2 (N - 1) T, velocity distribution
  *   or_run, all pairs       forces == or_forces_brute with rc = inf, NVE drift

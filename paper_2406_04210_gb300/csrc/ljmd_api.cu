@@ -119,6 +119,7 @@ struct md_box {
     int64_t prof_n[4] = {0, 0, 0, 0};
     // recorded forward run (md_integrate with ckpt_every > 0)
     bool rec_valid = false;
+    int64_t rec_serial = 0;    // serial number of the last recorded run
     int64_t rec_nsteps = 0;
     int rec_k = 0, rec_C = 0;
     double rec_dt = 0.0;
@@ -1223,6 +1224,7 @@ md_status md_integrate(md_box* b, double dt, int64_t nsteps, int32_t ckpt_every,
     }
     if (record) {
         b->rec_valid = true;
+        b->rec_serial += 1;
         b->rec_nsteps = nsteps;
         b->rec_k = ckpt_every;
         b->rec_C = (int)(nsteps / ckpt_every);
@@ -1524,6 +1526,7 @@ md_status md_get_info(md_box* b, md_info* out)
     i.device_bytes = bytes;
     i.rlist = b->rl;
     i.launches = b->launches;
+    i.record_id = b->rec_valid ? b->rec_serial : 0;
     if (b->lj_set) {
         std::vector<unsigned long long> nb(b->nrep);
         CK(b, cudaSetDevice(b->device));

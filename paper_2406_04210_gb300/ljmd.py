@@ -51,7 +51,8 @@ class Info(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("ncell_total", ctypes.c_int64),
                 ("rebuilds", ctypes.c_int64), ("steps", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64), ("rlist", ctypes.c_double),
-                ("launches", ctypes.c_int64), ("list_entries", ctypes.c_int64)]
+                ("launches", ctypes.c_int64), ("list_entries", ctypes.c_int64),
+                ("record_id", ctypes.c_int64)]
 
 
 _lock = threading.Lock()
@@ -419,7 +420,10 @@ class TrajectoryFn:
     Forward: md_set_state(x0, v0), md_set_lj(eps, sigma) (monatomic: scalar
     tensors; the box's cutoff and skin are kept), then a recorded
     md_integrate.  Backward: md_adjoint.  x0, v0 are (n, 3) float64 CUDA
-    tensors; eps, sigma are 0-d float64 tensors."""
+    tensors; eps, sigma are 0-d float64 tensors.  The box keeps one record:
+    a backward whose forward record was replaced (another forward on the same
+    box, a state or parameter change) raises MDError(MD_ERR_STATE) instead of
+    differentiating the other run."""
 
     _fn = None
 
@@ -439,11 +443,15 @@ class TrajectoryFn:
                     box._check(box._lib.md_get_state(box._h, xT.data_ptr(), vT.data_ptr(), None),
                                "md_get_state")
                     ctx.box = box
+                    ctx.record = box.info().record_id
                     return xT, vT
 
                 @staticmethod
                 def backward(ctx, gx, gv):
                     box = ctx.box
+                    if box.info().record_id != ctx.record:
+                        raise MDError(8, "TrajectoryFn.backward: the box no longer holds this forward "
+                                         "run's record (another forward, state or parameter change)")
                     gx = torch.zeros_like(gv) if gx is None else gx.contiguous()
                     gv = torch.zeros_like(gx) if gv is None else gv.contiguous()
                     lx0, lv0, ge, gs = box.adjoint(gx, gv)
@@ -457,9 +465,19 @@ class TrajectoryFn:
         return cls._fn.apply(*args)
 
 
+def _holds(box, x):
+    """Raise ValueError unless the box's current positions are x."""
+    torch = _torch()
+    cur = torch.empty((box.n_total, 3), dtype=torch.float64, device=x.device)
+    box._check(box._lib.md_get_state(box._h, cur.data_ptr(), None, None), "md_get_state")
+    if not torch.equal(cur, x.detach().to(torch.float64).reshape(-1, 3)):
+        raise ValueError("PairHistLossFn: x is not the state the box holds")
+
+
 class PairHistLossFn:
-    """loss = mean_k (h_k(x) - target_k)^2 of the box's current positions
-    (which must be x, e.g. the x_T a TrajectoryFn returned)."""
+    """loss = mean_k (h_k(x) - target_k)^2 of the box's current positions,
+    which must be x (e.g. the x_T a TrajectoryFn returned): forward and
+    backward check that the box still holds x and raise ValueError if not."""
 
     _fn = None
 
@@ -471,16 +489,19 @@ class PairHistLossFn:
             class _F(torch.autograd.Function):
                 @staticmethod
                 def forward(ctx, x, box, target, nbins, rhist, width, rmax):
+                    _holds(box, x)
                     h, _ = box.pair_hist(nbins, rhist, width, rmax)
                     t = target.detach().cpu().numpy().reshape(1, -1)
                     diff = h - t
                     ctx.box, ctx.args, ctx.diff = box, (nbins, rhist, width, rmax), diff
+                    ctx.save_for_backward(x)
                     return torch.tensor(float(np.mean(diff * diff)), dtype=torch.float64,
                                         device=x.device)
 
                 @staticmethod
                 def backward(ctx, g):
                     nbins, rhist, width, rmax = ctx.args
+                    _holds(ctx.box, ctx.saved_tensors[0])
                     coef = 2.0 * ctx.diff / nbins * float(g)
                     _, grad = ctx.box.pair_hist(nbins, rhist, width, rmax, coef=coef)
                     return (torch.from_numpy(grad).to(g.device), None, None, None, None, None, None)

@@ -152,3 +152,33 @@ def test_adjoint_requires_record(ljmd):
     with pytest.raises(ljmd.MDError) as ei:
         b.adjoint(np.zeros((s.n, 3)), np.zeros((s.n, 3)))
     assert ei.value.status == 8
+
+
+def test_autograd_backward_refuses_a_replaced_record(ljmd):
+    # two forwards on one box, then the first one's backward: the box holds
+    # only the second record, so the backward must fail rather than return
+    # the second run's gradients; the loss also refuses positions that are
+    # not the box's current state
+    import torch
+    s = inputs.fcc_system(4, seed=21)
+    b = ljmd.from_system(s, "mixed_ds")
+    target = torch.tensor(oracle.hist(s.box, s.pos) * 0.9)
+    x0 = torch.tensor(s.pos, device="cuda", requires_grad=True)
+    v0 = torch.tensor(s.vel, device="cuda", requires_grad=True)
+    eps = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+    sigma = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+    xa, va = ljmd.TrajectoryFn.apply(x0, v0, eps, sigma, b, s.dt, 10, 5)
+    rec_a = b.info().record_id
+    assert rec_a > 0
+    xb, vb = ljmd.TrajectoryFn.apply(x0, v0, eps, sigma, b, s.dt, 20, 5)
+    assert b.info().record_id > rec_a
+    with pytest.raises(ValueError):
+        ljmd.PairHistLossFn.apply(xa, b, target, 64, 2.5, 2.5 / 64, 2.8)
+    with pytest.raises(ljmd.MDError) as ei:
+        (xa * xa).sum().backward()
+    assert ei.value.status == 8
+    loss = ljmd.PairHistLossFn.apply(xb, b, target, 64, 2.5, 2.5 / 64, 2.8)
+    loss.backward()
+    assert torch.isfinite(x0.grad).all()
+    b.set_state(s.pos, s.vel)
+    assert b.info().record_id == 0

@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 import oracle
+from forcecheck import figures, pair_scale, report
 from paper_2406_04210_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -31,7 +32,7 @@ def neighbourhood(box, pos, i, radius, tree):
     return np.concatenate([[i], idx])
 
 
-def sampled_checks(b, s, lj, rl, nsample, rng, check_lists=True, tol=1e-5):
+def sampled_checks(b, s, lj, rl, nsample, rng, check_lists=True, tol=1e-5, name="sample"):
     from scipy.spatial import cKDTree
     f, _, _ = b.force()
     tree = cKDTree(np.mod(s.pos, s.box), boxsize=s.box)
@@ -40,6 +41,7 @@ def sampled_checks(b, s, lj, rl, nsample, rng, check_lists=True, tol=1e-5):
         count, nbr, pos_used = b.nlist()
         np.testing.assert_array_equal(pos_used, np.mod(s.pos, s.box))
     types = s.type
+    got_f, ref_f, scale = [], [], []
     for i in sample:
         idx = neighbourhood(s.box, s.pos, i, rl + 0.5, tree)
         sub = s.pos[idx]
@@ -53,12 +55,16 @@ def sampled_checks(b, s, lj, rl, nsample, rng, check_lists=True, tol=1e-5):
         for k in range(len(r2)):
             a, c = st[0], st[k + 1]
             S += abs(oracle.pair(lj.eps[a, c], lj.sigma[a, c], lj.rcut[a, c], 1, r2[k])[0]) * np.sqrt(r2[k])
+        got_f.append(f[i])
+        ref_f.append(fo[0])
+        scale.append(S)
         assert np.linalg.norm(f[i] - fo[0]) <= tol * S, i
         if check_lists:
             nl = oracle.nlist(s.box, sub, rl, use_cells=False)
             ref = np.sort(idx[nl.list[0, : nl.count[0]]])
             got = np.sort(nbr[i, : count[i]])
             assert np.array_equal(got, ref), i
+    report(name, figures(np.array(got_f), np.array(ref_f), np.array(scale)))
     return f
 
 
@@ -68,7 +74,7 @@ def test_lj4m_sampled_forces_lists_and_invariants(ljmd):
     b = ljmd.from_system(s, "mixed_ds")
     b.autotune(reps=2, cache=False)
     rng = np.random.default_rng(0)
-    f = sampled_checks(b, s, lj, 2.8, 200, rng)
+    f = sampled_checks(b, s, lj, 2.8, 200, rng, name="lj4m sample of 200")
     # Newton III over 4M particles (FP32 pair sums)
     assert np.abs(f.sum(axis=0)).max() <= 1e-7 * np.abs(f).sum()
     p0 = s.vel.sum(axis=0)
@@ -86,7 +92,8 @@ def test_binary256k_sampled_forces_and_lists(ljmd):
     for prec, tol in (("mixed_ds", 1e-5), ("fp64", 1e-12)):
         b = ljmd.from_system(s, prec)
         b.autotune(reps=2, cache=False)
-        sampled_checks(b, s, lj, float(s.rcut.max()) + s.skin, 100, np.random.default_rng(1), tol=tol)
+        sampled_checks(b, s, lj, float(s.rcut.max()) + s.skin, 100, np.random.default_rng(1), tol=tol,
+                       name=f"binary256k {prec} sample of 100")
         b.close()
 
 
@@ -108,7 +115,10 @@ def test_replicas512_sampled_replicas(ljmd):
         x = systems[r]
         lj = oracle.LJ(x.eps, x.sigma, x.rcut)
         fo, eo, _ = oracle.forces(x.box, x.pos, lj)
-        assert np.abs(f[off[r]:off[r + 1]] - fo).max() <= 1e-4 * np.abs(fo).max()
+        S = pair_scale(x.box, x.pos, lj)
+        fr = f[off[r]:off[r + 1]]
+        report(f"replicas512 replica {r} (N = {x.n})", figures(fr, fo, S))
+        assert (np.linalg.norm(fr - fo, axis=1) / S).max() <= 1e-5
         assert abs(e[r] - eo) <= 1e-5 * abs(eo)
         rr = oracle.run(x.box, x.pos, x.vel, lj, 0.3, 0.005, 10)
         d = p2[off[r]:off[r + 1]] - rr["pos"]

@@ -1,6 +1,6 @@
 """GPU parity of the CUDA path (through the C ABI) against the FP64 oracle.
 
-Tolerances (written here, derived in DESIGN.md "Tolerances"):
+Tolerances (the readings behind them are in tests/forcecheck.py):
   * neighbour sets: identical to the oracle's FP64 definition (bit-exact
     membership, compared after sorting by user index) in every precision;
   * forces: max_i |F_i - F_i^oracle| / S_i <= 1e-5 (FP32 pair forces) and
@@ -16,6 +16,7 @@ import numpy as np
 import pytest
 
 import oracle
+from forcecheck import figures, pair_scale, report
 from paper_2406_04210_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -38,25 +39,6 @@ def ljmd():
 
 def _lj(s):
     return oracle.LJ(s.eps, s.sigma, s.rcut, True)
-
-
-def pair_scale(box, pos, lj, types=None):
-    """S_i = sum_j |F_ij| over pairs within the cutoff (oracle pair function)."""
-    from scipy.spatial import cKDTree
-    n = pos.shape[0]
-    t = np.zeros(n, np.int32) if types is None else types
-    tree = cKDTree(np.mod(pos, box), boxsize=box)
-    pairs = tree.query_pairs(float(lj.rcut.max()) + 1e-9, output_type="ndarray")
-    d = pos[pairs[:, 0]] - pos[pairs[:, 1]]
-    d -= box * np.rint(d / box)
-    r2 = np.sum(d * d, axis=1)
-    S = np.zeros(n)
-    for k, (i, j) in enumerate(pairs):
-        f = oracle.pair(lj.eps[t[i], t[j]], lj.sigma[t[i], t[j]], lj.rcut[t[i], t[j]], 1, r2[k])[0]
-        m = abs(f) * np.sqrt(r2[k])
-        S[i] += m
-        S[j] += m
-    return S
 
 
 def thermo_close(th, ref, wabs, tol=1e-5):
@@ -85,6 +67,7 @@ def test_lj4000_lists_forces_energy(ljmd, prec):
     fo, eo, wo = oracle.forces(s.box, s.pos, lj)
     S = pair_scale(s.box, s.pos, lj)
     err = np.linalg.norm(f - fo, axis=1) / S
+    report(f"lj4000 {prec}", figures(f, fo, S))
     assert err.max() <= FTOL[prec], err.max()
     assert abs(e[0] - eo) <= ETOL[prec] * abs(eo)
     assert abs(w[0] - wo) <= ETOL[prec] * 0.5 * 2.5 * S.sum()
@@ -136,6 +119,7 @@ def test_binary_mixture_parity(ljmd):
         f, e, w = b.force()
         fo, eo, wo = oracle.forces(s.box, s.pos, lj, s.type)
         S = pair_scale(s.box, s.pos, lj, s.type)
+        report(f"binary3000 {prec}", figures(f, fo, S))
         assert (np.linalg.norm(f - fo, axis=1) / S).max() <= FTOL[prec]
         assert abs(e[0] - eo) <= ETOL[prec] * abs(eo)
         th = b.integrate(s.dt, 10)

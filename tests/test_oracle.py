@@ -376,6 +376,21 @@ def test_fire_relaxes():
 # Counter-based random numbers and the Andersen-like thermostat (Sec. 4: the
 # "Boltzmann" thermostat of the all-to-all workload), and the all-pairs form.
 # ---------------------------------------------------------------------------
+KAT = os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.txt")
+
+
+def test_philox_known_answer_vectors():
+    # Published known-answer vectors of Philox4x32-10 (Salmon et al., SC'11;
+    # Random123 distribution): they fix the multipliers, the Weyl key
+    # increments, the round count and the order of the output words
+    rows = [[int(x, 16) for x in ln.split()] for ln in open(KAT)
+            if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 3
+    for w in rows:
+        out = oracle.philox4x32(w[:4], w[4:6])
+        assert [int(x) for x in out] == w[6:], [hex(int(x)) for x in out]
+
+
 def test_philox_uniform_independent_and_mixing():
     key = (1234, 5678)
     words = np.concatenate([oracle.philox4x32((i, 0, 0, 0), key) for i in range(16384)]).astype(np.int64)
