@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(LJ_FORCE_THREADS) k_hvp_f32(BoxDev b, const fl
         const double wgt = *weight;
         if (MONO) {
             // one (d/deps, d/dsigma) share per warp and chunk (no block barrier)
-            const double de = warp_sum_d((double)ge), ds = warp_sum_d((double)gs);
+            const double de = warp_sum_ds(ge), ds = warp_sum_ds(gs);   // double-single warp sums
             if ((threadIdx.x & 31) == 0) {
                 const size_t q = (size_t)w * LJ_FORCE_WARPS + (threadIdx.x >> 5);
                 part_g[2 * q] += wgt * de;

@@ -211,10 +211,11 @@ __global__ void __launch_bounds__(LJ_FORCE_THREADS, SINGLE ? 8 : 6) k_force_f32(
         }
         if (ENERGY) {
             // one (E_pot, W) share per warp and chunk, no block barrier: the
-            // warps of a block run ahead into the next chunk independently
-            double de = 0.5 * (double)e, dw = 0.5 * (double)vir;
-            de = warp_sum_d(de);
-            dw = warp_sum_d(dw);
+            // warps of a block run ahead into the next chunk independently.
+            // The warp sum is double-single (two FP32 words per partial
+            // sum): FP64-class precision on the FP32 pipe, since FP64 adds
+            // are scarce on this GPU
+            const double de = 0.5 * warp_sum_ds(e), dw = 0.5 * warp_sum_ds(vir);
             if ((threadIdx.x & 31) == 0) {
                 const size_t q = (size_t)w * LJ_FORCE_WARPS + (threadIdx.x >> 5);
                 b.part_f[2 * q] = de;

@@ -64,6 +64,7 @@ __global__ void __launch_bounds__(LJ_CHUNK) k_integrate(BoxDev b, double dt, int
         int r = ch.x;
         int p = ch.y + (int)threadIdx.x;
         double ek = 0.0;
+        float ekf = 0.f;   // double-single state: FP32 per particle
         unsigned dmax = 0u;
         if (p < ch.z) {
             double F[3];
@@ -84,7 +85,6 @@ __global__ void __launch_bounds__(LJ_CHUNK) k_integrate(BoxDev b, double dt, int
             if (TSTAT && MODE != LJ_STEP_FIRST)
                 hit = tstat_collide(b, b.rep[r], r, p, *b.step_ctr + sidx, g);
             if (ACC == 0) {
-                float ekf = 0.f;
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     float vh = velf[c * np + p], vl = velf[3 * np + c * np + p];
@@ -107,7 +107,6 @@ __global__ void __launch_bounds__(LJ_CHUNK) k_integrate(BoxDev b, double dt, int
                     velf[c * np + p] = vh;
                     velf[3 * np + c * np + p] = vl;
                 }
-                ek = (double)ekf;
             } else {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
@@ -143,8 +142,9 @@ __global__ void __launch_bounds__(LJ_CHUNK) k_integrate(BoxDev b, double dt, int
             }
         }
         if (ENERGY && MODE != LJ_STEP_FIRST) {
-            // one E_kin share per warp and chunk (no block barrier)
-            const double s = warp_sum_d(0.5 * ek);
+            // one E_kin share per warp and chunk (no block barrier); the
+            // double-single state sums its FP32 squares in double-single
+            const double s = ACC == 0 ? 0.5 * warp_sum_ds(ekf) : warp_sum_d(0.5 * ek);
             if ((threadIdx.x & 31) == 0) b.part_k[(size_t)w * LJ_KIN_WARPS + (threadIdx.x >> 5)] = s;
         }
     }

@@ -236,6 +236,21 @@ __device__ __forceinline__ void ds_from_double(double x, float& h, float& l)
     l = __double2float_rn(x - (double)h);
 }
 
+// Sum over the warp in double-single arithmetic (FP32 pairs, Knuth's
+// two-sum at every step), returned as FP64 in every lane: an FP64-class sum
+// on the FP32 pipe (FP64 adds are scarce on this GPU).  The butterfly order
+// is fixed, so the result is deterministic.
+__device__ __forceinline__ double warp_sum_ds(float x)
+{
+    float h = x, l = 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, h, o), ol = __shfl_xor_sync(0xffffffffu, l, o);
+        ds_add_ds(h, l, oh, ol);
+    }
+    return (double)h + (double)l;
+}
+
 // Cheap block-level early exit of the rebuild kernels: nothing to do unless
 // the integrator or the host raised the box-wide request word.
 __device__ __forceinline__ bool box_needs_rebuild(const BoxDev& b)

@@ -465,12 +465,17 @@ class TrajectoryFn:
         return cls._fn.apply(*args)
 
 
-def _holds(box, x):
-    """Raise ValueError unless the box's current positions are x."""
+def _holds(box, x, tol=1e-8):
+    """Raise ValueError unless the box's current positions are x (to within
+    `tol`, minimum image: a list rebuild re-centres the stored offsets, which
+    moves the positions by rounding only)."""
     torch = _torch()
     cur = torch.empty((box.n_total, 3), dtype=torch.float64, device=x.device)
     box._check(box._lib.md_get_state(box._h, cur.data_ptr(), None, None), "md_get_state")
-    if not torch.equal(cur, x.detach().to(torch.float64).reshape(-1, 3)):
+    L = torch.as_tensor(np.repeat(box.box, box.n, axis=0), dtype=torch.float64, device=x.device)
+    d = cur - x.detach().to(torch.float64).reshape(-1, 3)
+    d = d - L * torch.round(d / L)
+    if d.numel() and float(d.abs().max()) > tol:
         raise ValueError("PairHistLossFn: x is not the state the box holds")
 
 
