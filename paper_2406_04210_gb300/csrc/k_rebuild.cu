@@ -643,7 +643,24 @@ __global__ void __launch_bounds__(LJ_LIST_THREADS, 3) k_nlist(BoxDev b)
     if (threadIdx.x == 0 && s_longest > 0) atomicMax(&b.err[2], s_longest);   // longest list of this build
 }
 
+// Condition of the step graph's list-update node: 1 when the integrator (or
+// the host) raised the box-wide rebuild word, so that steps without a build
+// launch none of the rebuild kernels; each 1 is counted (launch accounting).
+__global__ void k_set_rebuild_cond(cudaGraphConditionalHandle h, const int* any_req, unsigned long long* runs)
+{
+    const bool go = *((volatile const int*)any_req) != 0;
+    if (go) atomicAdd(runs, 1ull);
+    cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
 }  // namespace
+
+cudaError_t launch_set_rebuild_cond(cudaGraphConditionalHandle h, const BoxDev& b, unsigned long long* runs,
+                                    cudaStream_t s)
+{
+    k_set_rebuild_cond<<<1, 1, 0, s>>>(h, b.any_req, runs);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_bin(const BoxDev& b, int from_abs, Launch l)
 {

@@ -62,6 +62,11 @@ struct md_box {
     // the energy reduction's branch of the step graph (it overlaps the list update)
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // the rebuild sequence as the body of a conditional (IF) graph node
+    bool use_cond = true;
+    cudaStream_t cstream = nullptr;            // captures the node's body
+    unsigned long long* d_cond_runs = nullptr; // true conditions so far (device)
+    unsigned long long cond_runs_seen = 0;
     md_alloc_fn alloc = nullptr;
     md_free_fn free_ = nullptr;
     void* actx = nullptr;
@@ -305,20 +310,68 @@ md_status clear_err(md_box* b)
 // ------------------------------------------------------------------------
 // Rebuild / force sequences
 // ------------------------------------------------------------------------
-md_status enqueue_rebuild(md_box* b, int from_abs)
+// Kernels of one rebuild sequence (bin, scan x2, scatter, rank, gather,
+// list; all pairs: binning only re-wraps and re-centres).
+int rebuild_kernels(md_box* b) { return b->all_pairs ? 5 : 7; }
+
+md_status enqueue_rebuild(md_box* b, int from_abs, cudaStream_t s = nullptr)
 {
-    Launch l = lch(b);
+    if (!s) s = b->stream;
+    auto on = [s](Launch l) {
+        l.s = s;
+        return l;
+    };
+    Launch l = on(lch(b));
     CK(b, launch_bin(b->d, from_abs, l));
-    Launch lt{std::max(1, std::min((int)b->tiles.size(), b->nsm * 2)), 1024, b->stream};
+    Launch lt{std::max(1, std::min((int)b->tiles.size(), b->nsm * 2)), 1024, s};
     CK(b, launch_scan_tiles(b->d, b->d_tiles, (int)b->tiles.size(), b->d_tile_sum, lt));
     CK(b, launch_scatter(b->d, l));
-    CK(b, launch_sortgather(b->d, b->all_pairs ? lch(b) : lcell(b), lch(b)));
-    if (b->all_pairs) {
-        b->launches += 5;   // all pairs: binning only re-wraps and re-centres
-        return MD_OK;
-    }
-    CK(b, launch_nlist(b->d, llist(b)));
-    b->launches += 7;   // bin, scan x2, scatter, rank, gather, list
+    CK(b, launch_sortgather(b->d, on(b->all_pairs ? lch(b) : lcell(b)), l));
+    if (!b->all_pairs) CK(b, launch_nlist(b->d, on(llist(b))));
+    b->launches += rebuild_kernels(b);
+    return MD_OK;
+}
+
+// The list update of one step inside a captured step graph: a one-thread
+// kernel sets the condition of an IF node from the box-wide rebuild word,
+// and the node's body (captured on the box's second stream) holds the
+// rebuild sequence, so a step without a build launches one tiny kernel
+// instead of the whole sequence (whose kernels exit early anyway).  The
+// body's kernels are counted when they run (k_set_rebuild_cond counts the
+// true conditions in cond_runs).  Outside a capture, or if the graph API
+// refuses the node, the plain sequence is enqueued.
+md_status enqueue_rebuild_step(md_box* b)
+{
+    if (!b->use_cond) return enqueue_rebuild(b, 0);
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* edata = nullptr;
+    size_t nd = 0;
+    CK(b, cudaStreamGetCaptureInfo(b->stream, &cs, nullptr, &g, &deps, &edata, &nd));
+    if (cs != cudaStreamCaptureStatusActive) return enqueue_rebuild(b, 0);
+    cudaGraphConditionalHandle h;
+    CK(b, cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
+    CK(b, launch_set_rebuild_cond(h, b->d, b->d_cond_runs, b->stream));
+    b->launches += 1;
+    CK(b, cudaStreamGetCaptureInfo(b->stream, &cs, nullptr, &g, &deps, &edata, &nd));
+    cudaGraphNodeParams p{};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeIf;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(b, cudaGraphAddNode(&node, g, deps, edata, nd, &p));
+    CK(b, cudaStreamUpdateCaptureDependencies(b->stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    cudaGraph_t body = p.conditional.phGraph_out[0];
+    CK(b, cudaStreamBeginCaptureToGraph(b->cstream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    const int64_t l0 = b->launches;
+    md_status st = enqueue_rebuild(b, 0, b->cstream);
+    b->launches = l0;   // counted per execution instead
+    cudaGraph_t out = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(b->cstream, &out);
+    if (st != MD_OK) return st;
+    if (ce != cudaSuccess) return cuda_fail(b, ce, "cudaStreamEndCapture (rebuild body)");
     return MD_OK;
 }
 
@@ -545,7 +598,7 @@ md_status enqueue_steps(md_box* b, int64_t n, double dt, int energy, double* rin
         }
         if (s == n) break;
         CK(b, mark(s, 1, 0, b->stream));
-        CKS(enqueue_rebuild(b, 0));
+        CKS(enqueue_rebuild_step(b));
         CK(b, mark(s, 1, 1, b->stream));
         CK(b, join());
         CK(b, mark(s, 2, 0, b->stream));
@@ -631,18 +684,30 @@ md_status get_graph(md_box* b, int64_t n, double dt, int energy, cudaGraphExec_t
         ge.used.assign((size_t)(n + 1) * 4, 0);
         for (auto& e : ge.ev) CK(b, cudaEventCreate(&e));
     }
-    cudaGraph_t graph;
-    int64_t l0 = b->launches;
-    CK(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-    md_status st = enqueue_steps(b, n, dt, energy, b->d_thermo, b->profiling ? &ge : nullptr);
-    cudaError_t ce = cudaStreamEndCapture(b->stream, &graph);
-    ge.kernels = b->launches - l0;
-    b->launches = l0;
-    if (st != MD_OK) return st;
-    if (ce != cudaSuccess) return cuda_fail(b, ce, "cudaStreamEndCapture");
-    ce = cudaGraphInstantiate(&ge.exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (ce != cudaSuccess) return cuda_fail(b, ce, "cudaGraphInstantiate");
+    // with conditional list-update nodes first; should the runtime refuse
+    // them, once more with the plain (early-exit) rebuild sequence
+    for (;;) {
+        cudaGraph_t graph = nullptr;
+        int64_t l0 = b->launches;
+        CK(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        md_status st = enqueue_steps(b, n, dt, energy, b->d_thermo, b->profiling ? &ge : nullptr);
+        cudaError_t ce = cudaStreamEndCapture(b->stream, &graph);
+        ge.kernels = b->launches - l0;
+        b->launches = l0;
+        if (st == MD_OK && ce == cudaSuccess) {
+            ce = cudaGraphInstantiate(&ge.exec, graph, 0);
+            cudaGraphDestroy(graph);
+            graph = nullptr;
+            if (ce == cudaSuccess) break;
+        }
+        if (graph) cudaGraphDestroy(graph);
+        if (!b->use_cond) {
+            if (st != MD_OK) return st;
+            return cuda_fail(b, ce, "step graph capture");
+        }
+        cudaGetLastError();
+        b->use_cond = false;
+    }
     b->graphs.push_back(ge);
     *out = ge.exec;
     return MD_OK;
@@ -753,8 +818,10 @@ md_status md_batch_create(md_box** out, int32_t nrep, const int64_t* n, const do
         cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess ||
         cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&b->cstream, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
+        if (b->ev_join) cudaEventDestroy(b->ev_join);
         if (b->ev_fork) cudaEventDestroy(b->ev_fork);
         if (b->side) cudaStreamDestroy(b->side);
         if (b->ev) cudaEventDestroy(b->ev);
@@ -839,6 +906,7 @@ md_status md_batch_create(md_box** out, int32_t nrep, const int64_t* n, const do
         d.tstat_thr = 0u;
         CKS(dev_alloc(b, &d.nbuild, nrep));
         CKS(dev_alloc(b, &d.err, 4));
+        CKS(dev_alloc(b, &b->d_cond_runs, 1));
         CKS(dev_alloc(b, &d.part_k, LJ_KIN_WARPS * std::max<size_t>(1, b->chunks.size())));
         CKS(dev_alloc(b, &d.part_f, 2 * LJ_FORCE_WARPS * std::max<size_t>(1, b->chunks.size())));
         d.pf_stride = prec == MD_PREC_FP64 ? LJ_F64_WARPS : LJ_FORCE_WARPS;
@@ -890,6 +958,7 @@ md_status md_box_destroy(md_box* b)
     if (b->ev_fork) cudaEventDestroy(b->ev_fork);
     if (b->ev_join) cudaEventDestroy(b->ev_join);
     if (b->side) cudaStreamDestroy(b->side);
+    if (b->cstream) cudaStreamDestroy(b->cstream);
     if (b->stream) cudaStreamDestroy(b->stream);
     delete b;
     return MD_OK;
@@ -1181,8 +1250,13 @@ md_status md_integrate(md_box* b, double dt, int64_t nsteps, int32_t ckpt_every,
         cudaGraphExec_t g;
         CKS(get_graph(b, n, dt, energy, &g));
         CK(b, cudaGraphLaunch(g, b->stream));
+        unsigned long long runs = 0;
+        CK(b, cudaMemcpyAsync(&runs, b->d_cond_runs, sizeof runs, cudaMemcpyDeviceToHost, b->stream));
         int e2[3];
         CKS(read_err(b, e2));
+        // rebuild sequences the step graph's IF nodes ran
+        b->launches += (int64_t)(runs - b->cond_runs_seen) * rebuild_kernels(b);
+        b->cond_runs_seen = runs;
         for (auto& ge : b->graphs)
             if (ge.exec == g) {
                 b->launches += ge.kernels;
@@ -1345,8 +1419,12 @@ md_status md_adjoint(md_box* b, const double* lam_x_T, const double* lam_v_T, do
         CKS(tape_save(b, 0));
         if (!graphs.g[4]) CKS(capture(4, [&]() { return enqueue_steps(b, k, h, 0, nullptr, nullptr, true); }));
         CKS(launch(4));
+        unsigned long long runs = 0;
+        CK(b, cudaMemcpyAsync(&runs, b->d_cond_runs, sizeof runs, cudaMemcpyDeviceToHost, b->stream));
         int e2[3];
         CKS(read_err(b, e2));
+        b->launches += (int64_t)(runs - b->cond_runs_seen) * rebuild_kernels(b);   // the replay's rebuilds
+        b->cond_runs_seen = runs;
         if (e2[0]) return fail(b, MD_ERR_CAPACITY, "md_adjoint: replay of a segment failed");
         const int form = (c == C - 1 ? 1 : 0) | (c == 0 ? 2 : 0);
         if (!graphs.g[form]) CKS(capture(form, [&]() { return reverse(c == C - 1, c == 0); }));

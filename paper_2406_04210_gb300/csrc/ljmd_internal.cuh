@@ -490,6 +490,9 @@ int ljmd_scan_tile_cells();
 cudaError_t launch_scatter(const BoxDev& b, Launch l);
 cudaError_t launch_sortgather(const BoxDev& b, Launch l, Launch lg);   // rank (l), then gather (lg) unless all pairs
 cudaError_t launch_nlist(const BoxDev& b, Launch l);
+// sets a step graph's IF-node condition from the box-wide rebuild word
+cudaError_t launch_set_rebuild_cond(cudaGraphConditionalHandle h, const BoxDev& b, unsigned long long* runs,
+                                    cudaStream_t s);
 
 // k_force.cu
 cudaError_t launch_force(const BoxDev& b, int energy, Launch l);
