@@ -366,6 +366,34 @@ def bench_temperature_sweep(ljmd, inputs, steps, temps=(0.5, 0.722, 1.0, 1.5, 2.
     return out
 
 
+def bench_layouts(ljmd, s, tuning, steps=100,
+                  layouts=((1.0, "zrun"), (1.0, "morton"), (1.15, "zrun"), (1.15, "morton"))):
+    """A/B of the cell layouts on the same fluid: cell edge over the list
+    radius, and the order inside cells (z runs, or a space-filling Morton
+    curve over 4 x 4 x 4 sub-cells).  Per layout: in-graph force and list-
+    update times per step over `steps` steps (CUDA events in the step graph),
+    and one forced list build (binning, sort, list) timed with CUDA events."""
+    import torch
+    b = ljmd.from_system(s, "mixed_ds")
+    b.set_tuning(**{k: v for k, v in tuning.items() if k in b.TUNING})
+    out = []
+    for sc, od in layouts:
+        b.set_layout(cell_scale=sc, order=od)
+        b.integrate(s.dt, 20, thermo=False)
+        b.set_profiling(True)
+        b.integrate(s.dt, steps)
+        prof = b.profile()
+        b.set_profiling(False)
+        ms_build, _ = timed_call(lambda: b.neighbour_update(force=True))
+        out.append({"cell_scale": sc, "order": od,
+                    "force_ms_per_step": prof["force"][0] / steps,
+                    "list_update_ms_per_step": prof["list_update"][0] / steps,
+                    "forced_build_ms": ms_build})
+    b.close()
+    torch.cuda.synchronize()
+    return {"workload": f"the timed fluid, {steps} steps per layout", "points": out}
+
+
 def bench_all_pairs(ljmd, inputs, steps_mixed, steps_fp64):
     """The paper's first workload (Sec. 4): untruncated LJ between all pairs,
     velocity-Verlet and the Andersen-like thermostat; N = 2000 (fcc sites,
@@ -387,7 +415,7 @@ def bench_all_pairs(ljmd, inputs, steps_mixed, steps_fp64):
     return out
 
 
-def _summary(prec, adj, batched, binary, drift, allp, tsweep):
+def _summary(prec, adj, batched, binary, drift, allp, tsweep, layouts=None):
     def g(d, *keys):
         for k in keys:
             if not isinstance(d, dict) or k not in d:
@@ -411,6 +439,9 @@ def _summary(prec, adj, batched, binary, drift, allp, tsweep):
     out["all_pairs_n2000"] = {"mixed_ds": r3(g(allp, "mixed_ds", "value")), "fp64": r3(g(allp, "fp64", "value"))}
     pts = g(tsweep, "points") or []
     out["tsweep_n100k"] = [[p["T"], r3(p["value"]), r3(p["rebuilds_per_step"])] for p in pts]
+    lay = g(layouts, "points") or []
+    out["layouts_force_list_build_ms"] = [[p["cell_scale"], p["order"], r3(p["force_ms_per_step"]),
+                                           r3(p["forced_build_ms"])] for p in lay]
     return out
 
 
@@ -527,6 +558,7 @@ def run_gpu(args):
         prec[p] = n * k / (ms2 / 1e3)
         b2.close()
 
+    layouts = _guarded(lambda: bench_layouts(ljmd, s, tuning)) if (args.layouts or not args.quick) else None
     adj = None if args.quick else bench_adjoint(ljmd, inputs)
     batched = None if args.quick else _guarded(lambda: bench_batched(ljmd, inputs, 1000))
     drift = None if args.quick else _guarded(lambda: bench_drift(ljmd, inputs, 100000))
@@ -567,11 +599,12 @@ def run_gpu(args):
                    "drift_per_particle": float((E[-1] - E[0]) / n)},
         "rebuilds_in_timed_region": int(info1.rebuilds - info0.rebuilds),
         "temperature_sweep": tsweep, "all_pairs": allp, "drift_lj4000": drift, "binary256k": binary,
+        "layouts": layouts,
         "adjoint": adj, "batched": batched, "tuning": tuning,
     }
     # the headline figures of the metric's second half and of the other
     # workloads, last in the line and compact
-    line["summary"] = _summary(prec, adj, batched, binary, drift, allp, tsweep)
+    line["summary"] = _summary(prec, adj, batched, binary, drift, allp, tsweep, layouts)
     print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
@@ -594,6 +627,8 @@ def main():
                     help="fcc cells per edge (100 = the 4.0M-particle workload; smaller for profiling)")
     ap.add_argument("--quick", action="store_true",
                     help="skip the other precisions and the CPU oracle (profiling runs)")
+    ap.add_argument("--layouts", action="store_true",
+                    help="with --quick: still run the cell-layout A/B")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -269,11 +269,35 @@ md_status md_get_info(md_box* b, md_info* out);
 md_status md_set_tuning(md_box* b, const int32_t t[4]);
 md_status md_get_tuning(md_box* b, int32_t t[4]);
 
+/* Cell layout, the binning's part of the tuning (Sec. 3: Verlet lists from a
+ * spatial decomposition, "particle binning"; particles sorted for
+ * locality):
+ *   cell_scale  cell edge over the list radius, >= 1 (default 1: the most
+ *               cells the 27-cell stencil allows, floor(L / rl) per
+ *               dimension; larger values give fewer, fuller cells)
+ *   order       order of the particles inside a cell: MD_ORDER_ZRUN (0,
+ *               default) by z offset from the cell centre, which lets the
+ *               list build take only the run of each neighbour cell within
+ *               reach along z; MD_ORDER_MORTON (1) by a space-filling (Morton)
+ *               curve over the cell's 4 x 4 x 4 sub-cells, then z, for
+ *               locality of the neighbour gathers (the list build then scans
+ *               whole neighbour cells)
+ * md_set_layout re-bins the particles and rebuilds the lists when either
+ * changes (results are unchanged up to FP32 summation order; the lists are
+ * the same sets).  Not in the all-pairs form (one cell per replica). */
+enum { MD_ORDER_ZRUN = 0, MD_ORDER_MORTON = 1 };
+md_status md_set_layout(md_box* b, double cell_scale, int32_t order);
+md_status md_get_layout(md_box* b, double* cell_scale, int32_t* order);
+
 /* Autotuner: times `reps` launches of the pair-force kernel for each
  * blocks-per-SM candidate, and `reps` forced list builds for each segment
  * length (automatic choice +-2) x list blocks-per-SM candidate, at the
  * current positions; applies the fastest and returns it in t[4] (as
- * md_get_tuning).  The box's state is unchanged apart from a list rebuild. */
+ * md_get_tuning).  It then times the cell layouts (cell_scale 1 and 1.15,
+ * each in both orders) as a step's cost -- one force evaluation plus a list
+ * build spread over the box's observed steps per build (10 before any
+ * step) -- and keeps the cheapest (md_get_layout reads it).  The box's state
+ * is unchanged apart from a list rebuild. */
 md_status md_autotune(md_box* b, int32_t reps, int32_t t[4]);
 
 /* Phase timing of md_integrate.  md_set_profiling(b, 1) resets the counters

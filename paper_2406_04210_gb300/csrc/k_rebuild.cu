@@ -233,17 +233,32 @@ __global__ void __launch_bounds__(LJ_CHUNK) k_scatter(BoxDev b)
 // user index (count of smaller keys; keys are unique), so the layout is a
 // deterministic function of the positions and the list build can take, in
 // every neighbour cell, the contiguous run of candidates within reach along
-// z.  The ranks are written as each member's final slot (dst); k_gather then
+// z.  The alternative layout (order 1) sorts a cell by a space-filling curve
+// over its 4 x 4 x 4 sub-cells first (Sec. 3: particles are sorted for
+// locality); the list build then takes whole neighbour cells.  The ranks are
+// written as each member's final slot (dst); k_gather then
 // moves the state into the sorted arrays, one thread per particle, and
 // derives the cell-relative offsets and their FP32 copy.  (All pairs: one
 // cell per replica, no order; k_sortgather gathers directly.)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ unsigned long long sort_key(const BoxDev& b, int p, double zc)
+__device__ __forceinline__ unsigned long long sort_key(const BoxDev& b, const RepDev& R, int p, const double* centre)
 {
-    const float z = __double2float_rn(b.xabsB[2 * b.np + p] - zc);
+    const float z = __double2float_rn(b.xabsB[2 * b.np + p] - centre[2]);
     const unsigned u = __float_as_uint(z);
     const unsigned ord = (u & 0x80000000u) ? ~u : (u | 0x80000000u);   // order-preserving
-    return ((unsigned long long)ord << 32) | (unsigned)b.uidB[p];
+    if (b.order == 0) return ((unsigned long long)ord << 32) | (unsigned)b.uidB[p];
+    // space-filling-curve order (Morton, or Z-order, curve over the cell's
+    // 4 x 4 x 4 sub-cells: the sub-cell coordinates' bits interleaved), then
+    // the z offset, then the user index (< 2^26) -- 6 + 32 + 26 bits
+    unsigned m = 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const double o = b.xabsB[c * b.np + p] - centre[c];
+        int sc = (int)floor((o * R.inv_ell[c] + 0.5) * 4.0);
+        sc = sc < 0 ? 0 : (sc > 3 ? 3 : sc);
+        m |= (unsigned)(sc & 1) << c | (unsigned)(sc >> 1) << (c + 3);
+    }
+    return ((unsigned long long)m << 58) | ((unsigned long long)ord << 26) | (unsigned)b.uidB[p];
 }
 
 // Gather particle p (old order) into slot q of cell gc, with the cell-
@@ -313,11 +328,11 @@ __global__ void __launch_bounds__(256) k_sortgather(BoxDev b)
             int idx = base + lane;
             int p = idx < n ? b.perm[s0 + idx] : -1;
             const unsigned long long none = ~0ull;
-            unsigned long long key = idx < n ? sort_key(b, p, centre[2]) : none;
+            unsigned long long key = idx < n ? sort_key(b, R, p, centre) : none;
             int rank = 0;
             for (int b2 = 0; b2 < n; b2 += 32) {
                 unsigned long long k2 =
-                    b2 == base ? key : ((b2 + lane < n) ? sort_key(b, b.perm[s0 + b2 + lane], centre[2]) : none);
+                    b2 == base ? key : ((b2 + lane < n) ? sort_key(b, R, b.perm[s0 + b2 + lane], centre) : none);
 #pragma unroll 8
                 for (int t = 0; t < 32; ++t) {
                     unsigned long long kt = __shfl_sync(0xffffffffu, k2, t);
@@ -491,7 +506,9 @@ __global__ void __launch_bounds__(LJ_LIST_THREADS, 3) k_nlist(BoxDev b)
                     zmin = fminf(zmin, pq[g].z);   // g >= nq repeats particle 0
                     zmax = fmaxf(zmax, pq[g].z);
                 }
-                if (!far) {
+                if (!far && b.order != 0) {
+                    len = rk.y - rk.x;   // space-filling-curve order: the whole cell
+                } else if (!far) {
                     // the cell is sorted by z offset: keep the run with
                     // z_j + shift_z within zreach of the quad's z range
                     const float zlo = zmin - zreach - sh.z, zhi = zmax + zreach - sh.z;
@@ -570,13 +587,13 @@ __global__ void __launch_bounds__(LJ_LIST_THREADS, 3) k_nlist(BoxDev b)
                     }
 #pragma unroll
                     for (int g = 0; g < 4; ++g) {
+                        if (g >= nq) break;   // warp-uniform: slots past the quad's end take nothing
                         bool in[2];
 #pragma unroll
                         for (int h = 0; h < 2; ++h) {
                             const float ddx = pq[g].x - qx[h], ddy = pq[g].y - qy[h], ddz = pq[g].z - qz[h];
                             const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                            // slots past the quad's end take nothing
-                            in[h] = r2 < hi2 && selfg[h] != g && g < nq;
+                            in[h] = r2 < hi2 && selfg[h] != g;
                             nearb[g] = nearb[g] || (in[h] && r2 >= lo2);
                         }
                         const unsigned b0 = __ballot_sync(0xffffffffu, in[0]);
@@ -584,8 +601,13 @@ __global__ void __launch_bounds__(LJ_LIST_THREADS, 3) k_nlist(BoxDev b)
                         const int pos0 = cnt[g] + __popc(b0 & lt_mask);
                         const int pos1 = cnt[g] + __popc(b0) + __popc(b1 & lt_mask);
                         uint32_t* const rg = row0 + (size_t)b.K * g;
-                        if (in[0] && pos0 < b.K) rg[pos0] = ent[0];
-                        if (in[1] && pos1 < b.K) rg[pos1] = ent[1];
+                        if (cnt[g] + 64 <= b.K) {   // warp-uniform: room for the whole pass
+                            if (in[0]) rg[pos0] = ent[0];
+                            if (in[1]) rg[pos1] = ent[1];
+                        } else {                    // entries beyond the capacity are counted only
+                            if (in[0] && pos0 < b.K) rg[pos0] = ent[0];
+                            if (in[1] && pos1 < b.K) rg[pos1] = ent[1];
+                        }
                         cnt[g] += __popc(b0) + __popc(b1);
                     }
                 }

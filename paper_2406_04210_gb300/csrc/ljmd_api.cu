@@ -114,6 +114,8 @@ struct md_box {
     // tuning
     int min_capacity = 0;
     bool autofit = false;      // fit the capacity after the next full build
+    double cell_scale = 1.0;   // cell edge / list radius (>= 1)
+    int order = 0;             // order inside a cell (MD_ORDER_*)
     int force_per_sm = 0;      // 0 = automatic (tuning)
     int list_per_sm = 0;
     int seg_cells = 0;
@@ -446,6 +448,75 @@ md_status make_segments(md_box* b, bool shrink)
     return MD_OK;
 }
 
+// The cell grid of every replica (particle binning, Sec. 3): floor(L / (rl *
+// cell_scale)) cells per dimension (cell_scale >= 1: every cell edge is at
+// least the list radius, as the 27-cell stencil needs), scan tiles, segments
+// and a list capacity for the densest replica.  The caller re-bins (full
+// rebuild) afterwards.
+md_status make_grid(md_box* b)
+{
+    BoxDev& d = b->d;
+    invalidate_graphs(b);
+    b->tiles.clear();
+    int cell_off = 0;
+    double maxdens = 0.0;
+    for (int r = 0; r < b->nrep; ++r) {
+        RepDev& R = b->reps[r];
+        for (int c = 0; c < 3; ++c) {
+            R.nc[c] = std::max(1, (int)std::floor(R.L[c] / (b->rl * b->cell_scale)));
+            R.ell[c] = R.L[c] / R.nc[c];
+            R.inv_ell[c] = (double)R.nc[c] / R.L[c];
+            R.ellf[c] = (float)R.ell[c];
+        }
+        R.cell_off = cell_off;
+        R.ncell = R.nc[0] * R.nc[1] * R.nc[2];
+        int first_tile = (int)b->tiles.size();
+        for (int c0 = 0; c0 < R.ncell; c0 += ljmd_scan_tile_cells())
+            b->tiles.push_back(make_int4(r, cell_off + c0,
+                                         cell_off + std::min(R.ncell, c0 + ljmd_scan_tile_cells()),
+                                         first_tile));
+        cell_off += R.ncell;
+        maxdens = std::max(maxdens, R.n / (R.L[0] * R.L[1] * R.L[2]));
+    }
+    d.ncell = cell_off;
+    d.ell1 = make_float3(b->reps[0].ellf[0], b->reps[0].ellf[1], b->reps[0].ellf[2]);
+    CK(b, cudaMemcpyAsync(b->d_rep, b->reps.data(), sizeof(RepDev) * b->reps.size(),
+                          cudaMemcpyHostToDevice, b->stream));
+    dev_release(b, d.cell_count);
+    dev_release(b, d.cell_start);
+    dev_release(b, d.cell_end);
+    dev_release(b, (void*)d.cell_rep);
+    dev_release(b, b->d_tiles);
+    dev_release(b, b->d_tile_sum);
+    d.cell_count = d.cell_start = d.cell_end = nullptr;
+    d.cell_rep = nullptr;
+    CKS(dev_alloc(b, &d.cell_count, d.ncell));
+    CKS(dev_alloc(b, &d.cell_start, d.ncell));
+    CKS(dev_alloc(b, &d.cell_end, d.ncell));
+    int* cr;
+    CKS(dev_alloc(b, &cr, d.ncell, false));
+    {
+        std::vector<int> hc(d.ncell);
+        for (int r = 0; r < b->nrep; ++r)
+            for (int c = 0; c < b->reps[r].ncell; ++c) hc[b->reps[r].cell_off + c] = r;
+        CK(b, cudaMemcpyAsync(cr, hc.data(), sizeof(int) * d.ncell, cudaMemcpyHostToDevice, b->stream));
+        CK(b, cudaStreamSynchronize(b->stream));
+    }
+    d.cell_rep = cr;
+    CKS(dev_alloc(b, &b->d_tiles, b->tiles.size(), false));
+    CKS(dev_alloc(b, &b->d_tile_sum, b->tiles.size()));
+    CK(b, cudaMemcpyAsync(b->d_tiles, b->tiles.data(), sizeof(int4) * b->tiles.size(),
+                          cudaMemcpyHostToDevice, b->stream));
+    CKS(make_segments(b, false));
+    // list capacity: expected neighbours at the densest replica, +30 %
+    double expect = b->all_pairs ? 0.0 : maxdens * 4.18879020478639 * b->rl * b->rl * b->rl;
+    int K = round_up((int64_t)(1.3 * expect) + 16, 8);   // all pairs: no lists, a token row
+    if (b->min_capacity > 0) K = round_up(b->min_capacity, 8);
+    CKS(alloc_lists(b, K));
+    b->autofit = true;
+    return MD_OK;
+}
+
 // Rebuild all replicas now (forced), regrowing the lists until they fit,
 // then recompute the forces.
 md_status full_rebuild(md_box* b)
@@ -459,6 +530,12 @@ md_status full_rebuild(md_box* b)
         b->binned = true;
         if (e2[0] & LJ_ERRBIT_TIMEOUT) return fail(b, MD_ERR_TIMEOUT, "list build: device wait timed out");
         if (e2[0] & LJ_ERRBIT_TILE) {
+            bool can_shrink = false;
+            for (const RepDev& R : b->reps) can_shrink = can_shrink || R.S > 1;
+            if (!can_shrink)
+                return fail(b, MD_ERR_CAPACITY,
+                            "list build: the 27 cells around one cell hold more than 2048 particles "
+                            "(cells too large for the density)");
             CKS(make_segments(b, true));
             continue;
         }
@@ -484,6 +561,42 @@ md_status full_rebuild(md_box* b)
         return MD_OK;
     }
     return fail(b, MD_ERR_CAPACITY, "neighbour list kept overflowing");
+}
+
+// Apply a cell layout (cell scale, order inside cells): a new cell grid
+// when the scale changes (positions first put back into xabs), then a full
+// rebuild in the new order.  The box's positions are unchanged.
+static md_status apply_layout(md_box* b, double scale, int order)
+{
+    b->order = order;
+    b->d.order = order;
+    invalidate_graphs(b);
+    if (scale != b->cell_scale) {
+        b->cell_scale = scale;
+        if (!b->fresh_abs) {
+            CK(b, launch_materialize(b->d, lch(b)));
+            b->fresh_abs = true;
+        }
+        CKS(make_grid(b));
+    }
+    b->rec_valid = false;
+    return full_rebuild(b);
+}
+
+// A layout whose lists cannot be built (a 27-cell tile over 2048 particles)
+// is refused: the previous layout is put back and its lists rebuilt, and the
+// refusal's status and message are returned.
+md_status set_layout(md_box* b, double scale, int order)
+{
+    if (scale == b->cell_scale && order == b->order) return MD_OK;
+    const double old_scale = b->cell_scale;
+    const int old_order = b->order;
+    const md_status st = apply_layout(b, scale, order);
+    if (st == MD_OK || st != MD_ERR_CAPACITY) return st;
+    const std::string why = b->err;
+    CKS(clear_err(b));
+    CKS(apply_layout(b, old_scale, old_order));
+    return fail(b, st, why);
 }
 
 md_status snapshot_setup(md_box* b)
@@ -1069,66 +1182,7 @@ md_status md_set_lj(md_box* b, int32_t ntypes, const double* eps, const double* 
     d.band = (float)(1.5e-4 * rl * rl);
     double thr = 0.5 * skin - 2e-6;
     d.disp_thr2 = thr > 0 ? (float)(thr * thr) : 0.0f;
-    if (grid_changes) {
-        invalidate_graphs(b);
-        b->tiles.clear();
-        int cell_off = 0;
-        double maxdens = 0.0;
-        for (int r = 0; r < b->nrep; ++r) {
-            RepDev& R = b->reps[r];
-            for (int c = 0; c < 3; ++c) {
-                R.nc[c] = std::max(1, (int)std::floor(R.L[c] / rl));
-                R.ell[c] = R.L[c] / R.nc[c];
-                R.inv_ell[c] = (double)R.nc[c] / R.L[c];
-                R.ellf[c] = (float)R.ell[c];
-            }
-            R.cell_off = cell_off;
-            R.ncell = R.nc[0] * R.nc[1] * R.nc[2];
-            int first_tile = (int)b->tiles.size();
-            for (int c0 = 0; c0 < R.ncell; c0 += ljmd_scan_tile_cells())
-                b->tiles.push_back(make_int4(r, cell_off + c0,
-                                             cell_off + std::min(R.ncell, c0 + ljmd_scan_tile_cells()),
-                                             first_tile));
-            cell_off += R.ncell;
-            maxdens = std::max(maxdens, R.n / (R.L[0] * R.L[1] * R.L[2]));
-        }
-        d.ncell = cell_off;
-        d.ell1 = make_float3(b->reps[0].ellf[0], b->reps[0].ellf[1], b->reps[0].ellf[2]);
-        CK(b, cudaMemcpyAsync(b->d_rep, b->reps.data(), sizeof(RepDev) * b->reps.size(),
-                              cudaMemcpyHostToDevice, b->stream));
-        dev_release(b, d.cell_count);
-        dev_release(b, d.cell_start);
-        dev_release(b, d.cell_end);
-        dev_release(b, (void*)d.cell_rep);
-        dev_release(b, b->d_tiles);
-        dev_release(b, b->d_tile_sum);
-        d.cell_count = d.cell_start = d.cell_end = nullptr;
-        d.cell_rep = nullptr;
-        CKS(dev_alloc(b, &d.cell_count, d.ncell));
-        CKS(dev_alloc(b, &d.cell_start, d.ncell));
-        CKS(dev_alloc(b, &d.cell_end, d.ncell));
-        int* cr;
-        CKS(dev_alloc(b, &cr, d.ncell, false));
-        {
-            std::vector<int> hc(d.ncell);
-            for (int r = 0; r < b->nrep; ++r)
-                for (int c = 0; c < b->reps[r].ncell; ++c) hc[b->reps[r].cell_off + c] = r;
-            CK(b, cudaMemcpyAsync(cr, hc.data(), sizeof(int) * d.ncell, cudaMemcpyHostToDevice, b->stream));
-            CK(b, cudaStreamSynchronize(b->stream));
-        }
-        d.cell_rep = cr;
-        CKS(dev_alloc(b, &b->d_tiles, b->tiles.size(), false));
-        CKS(dev_alloc(b, &b->d_tile_sum, b->tiles.size()));
-        CK(b, cudaMemcpyAsync(b->d_tiles, b->tiles.data(), sizeof(int4) * b->tiles.size(),
-                              cudaMemcpyHostToDevice, b->stream));
-        CKS(make_segments(b, false));
-        // list capacity: expected neighbours at the densest replica, +30 %
-        double expect = all_pairs ? 0.0 : maxdens * 4.18879020478639 * rl * rl * rl;
-        int K = round_up((int64_t)(1.3 * expect) + 16, 8);   // all pairs: no lists, a token row
-        if (b->min_capacity > 0) K = round_up(b->min_capacity, 8);
-        CKS(alloc_lists(b, K));
-        b->autofit = true;
-    }
+    if (grid_changes) CKS(make_grid(b));
     b->lj_set = true;
     b->rec_valid = false;
     CKS(full_rebuild(b));
@@ -1728,8 +1782,76 @@ md_status md_autotune(md_box* b, int32_t reps, int32_t t[4])
     b->list_per_sm = best_l;
     CKS(make_segments(b, false));
     CKS(full_rebuild(b));
+    // cell layout: a step's cost (one force evaluation, plus one list build
+    // spread over the observed steps per build) for each candidate
+    {
+        unsigned long long nb = 0;
+        std::vector<unsigned long long> nbv(b->nrep);
+        CK(b, cudaMemcpyAsync(nbv.data(), b->d.nbuild, sizeof(unsigned long long) * b->nrep, cudaMemcpyDeviceToHost,
+                              b->stream));
+        CK(b, cudaStreamSynchronize(b->stream));
+        for (auto v : nbv) nb = std::max(nb, v);
+        const double spb = (b->steps > 0 && nb > 2) ? std::max(1.0, (double)b->steps / (double)(nb - 2)) : 10.0;
+        const double scales[2] = {1.0, 1.15};
+        double best_cost = 1e300, best_scale = b->cell_scale;
+        int best_order = b->order;
+        for (double sc : scales)
+            for (int od = 0; od < 2; ++od) {
+                const md_status st = set_layout(b, sc, od);
+                if (st == MD_ERR_CAPACITY) continue;   // its tiles overflow: not a candidate
+                if (st != MD_OK) return st;
+                float ms_f, ms_b;
+                CKS(time_launches(b, reps, [&]() -> md_status { return enqueue_force(b, 1, nullptr); }, &ms_f));
+                CKS(time_launches(b, reps, [&]() -> md_status {
+                    CKS(set_all_rebuild(b));
+                    return enqueue_rebuild(b, b->fresh_abs ? 1 : 0);
+                }, &ms_b));
+                int e2[3];
+                CKS(read_err(b, e2));
+                if (e2[0] & (LJ_ERRBIT_TILE | LJ_ERRBIT_CAPACITY)) {
+                    CKS(clear_err(b));
+                    CKS(full_rebuild(b));   // regrow, then time this layout again
+                    CKS(time_launches(b, reps, [&]() -> md_status {
+                        CKS(set_all_rebuild(b));
+                        return enqueue_rebuild(b, b->fresh_abs ? 1 : 0);
+                    }, &ms_b));
+                }
+                const double cost = ms_f + ms_b / spb;
+                if (cost < best_cost) {
+                    best_cost = cost;
+                    best_scale = sc;
+                    best_order = od;
+                }
+            }
+        CKS(set_layout(b, best_scale, best_order));
+    }
     CKS(leave(b));
     return md_get_tuning(b, t);
+}
+
+md_status md_set_layout(md_box* b, double cell_scale, int32_t order)
+{
+    if (!b || !(cell_scale >= 1.0) || !std::isfinite(cell_scale) || order < 0 || order > 1)
+        return fail(b, MD_ERR_ARG, "md_set_layout: cell_scale must be >= 1 and order 0 or 1");
+    if (b->all_pairs) return fail(b, MD_ERR_ARG, "md_set_layout: not in the all-pairs form");
+    if (!b->lj_set) {   // applied by md_set_lj
+        b->cell_scale = cell_scale;
+        b->order = order;
+        b->d.order = order;
+        return MD_OK;
+    }
+    CKS(enter(b));
+    CKS(set_layout(b, cell_scale, order));
+    CKS(leave(b));
+    return MD_OK;
+}
+
+md_status md_get_layout(md_box* b, double* cell_scale, int32_t* order)
+{
+    if (!b) return MD_ERR_ARG;
+    if (cell_scale) *cell_scale = b->cell_scale;
+    if (order) *order = b->order;
+    return MD_OK;
 }
 
 }  // extern "C"

@@ -179,6 +179,7 @@ struct BoxDev {
     const double* tstat_T;
     long long* step_ctr;       // steps since md_set_thermostat (device word)
     int all_pairs;             // every cutoff infinite: forces over all pairs, no lists
+    int order;                 // order inside a cell: 0 z runs (LJ_ORDER_ZRUN), 1 Morton sub-cells
     int ap_js;                 // all pairs: slices of the j range per chunk
     float4* ap_part;           // [slice][slot] partial FP32 forces
     double* ap_part64;         // [slice][3][slot] partial FP64 forces

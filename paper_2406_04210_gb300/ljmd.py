@@ -29,7 +29,7 @@ STATUS = {0: "MD_OK", 1: "MD_ERR_ARG", 2: "MD_ERR_CUDA", 3: "MD_ERR_OOM", 4: "MD
 EXPORTS = ["md_set_allocator", "md_batch_create", "md_box_create", "md_box_destroy",
            "md_set_lj", "md_neighbour_update", "md_force", "md_integrate", "md_adjoint",
            "md_get_state", "md_set_state", "md_get_nlist", "md_get_info", "md_set_tuning",
-           "md_get_tuning", "md_autotune",
+           "md_get_tuning", "md_autotune", "md_set_layout", "md_get_layout",
            "md_set_profiling", "md_get_profile", "md_pair_hist", "md_force_noalloc",
            "md_set_thermostat",
            "md_last_error", "md_status_string"]
@@ -94,6 +94,8 @@ def load(path: str | None = None):
         L.md_set_tuning.argtypes = [vp, vp]
         L.md_get_tuning.argtypes = [vp, vp]
         L.md_autotune.argtypes = [vp, i32, vp]
+        L.md_set_layout.argtypes = [vp, d, i32]
+        L.md_get_layout.argtypes = [vp, vp, vp]
         L.md_set_profiling.argtypes = [vp, i32]
         L.md_pair_hist.argtypes = [vp, i32, d, d, d, vp, vp, vp]
         L.md_force_noalloc.argtypes = [vp, vp, vp, vp]
@@ -330,6 +332,23 @@ class Box:
         t = np.array([cur[k] for k in self.TUNING], dtype=np.int32)
         self._check(self._lib.md_set_tuning(self._h, t.ctypes.data), "md_set_tuning")
 
+    ORDERS = {"zrun": 0, "morton": 1}
+
+    def layout(self):
+        """The cell layout: {"cell_scale": float, "order": "zrun" | "morton"}."""
+        sc = ctypes.c_double()
+        od = ctypes.c_int32()
+        self._check(self._lib.md_get_layout(self._h, ctypes.byref(sc), ctypes.byref(od)), "md_get_layout")
+        return {"cell_scale": sc.value, "order": {v: k for k, v in self.ORDERS.items()}[od.value]}
+
+    def set_layout(self, cell_scale=None, order=None):
+        """Cell edge over the list radius (>= 1) and the order inside cells
+        ("zrun" or "morton"); unspecified values keep their current setting."""
+        cur = self.layout()
+        sc = cur["cell_scale"] if cell_scale is None else float(cell_scale)
+        od = self.ORDERS[cur["order"] if order is None else order]
+        self._check(self._lib.md_set_layout(self._h, sc, od), "md_set_layout")
+
     def autotune(self, reps=5, cache=True):
         """Measure and apply the fastest launch/layout settings (md_autotune).
         With cache, results are kept per (GPU, replicas, log2 N, density) in
@@ -354,11 +373,16 @@ class Box:
             except Exception:
                 table = {}
             if key in table:
-                self.set_tuning(**table[key])
+                ent = dict(table[key])
+                lay = {k: ent.pop(k) for k in ("cell_scale", "order") if k in ent}
+                self.set_tuning(**ent)
+                if lay:
+                    self.set_layout(**lay)
                 return table[key]
         t = np.zeros(4, dtype=np.int32)
         self._check(self._lib.md_autotune(self._h, int(reps), t.ctypes.data), "md_autotune")
         res = dict(zip(self.TUNING, (int(x) for x in t)))
+        res.update(self.layout())
         if cache and path:
             try:
                 os.makedirs(os.path.dirname(path), exist_ok=True)

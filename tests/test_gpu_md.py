@@ -285,3 +285,51 @@ def test_autotune_keeps_results(ljmd):
     d = b.get_state()[0] - r["pos"]
     d -= s.box * np.rint(d / s.box)
     assert np.abs(d).max() <= 1e-4
+
+
+@pytest.mark.parametrize("scale,order", [(1.0, "morton"), (1.3, "zrun"), (1.3, "morton")])
+def test_cell_layouts_keep_lists_forces_and_trajectories(ljmd, scale, order):
+    # the binning's layout options (cell edge over the list radius, order
+    # inside cells) change neither the lists (the FP64 definition) nor, beyond
+    # FP32 summation order, the forces and trajectories
+    s = inputs.lj4000()
+    b = ljmd.from_system(s, "mixed_ds")
+    b.set_layout(cell_scale=scale, order=order)
+    assert b.layout() == {"cell_scale": scale, "order": order}
+    check_lists(b, s, 2.8)
+    f, e, w = b.force()
+    lj = _lj(s)
+    fo, eo, wo = oracle.forces(s.box, s.pos, lj)
+    S = pair_scale(s.box, s.pos, lj)
+    assert (np.linalg.norm(f - fo, axis=1) / S).max() <= 1e-5
+    assert abs(e[0] - eo) <= 1e-5 * abs(eo)
+    b.integrate(s.dt, 10)
+    pos, vel, img = b.get_state()
+    r = oracle.run(s.box, s.pos, s.vel, lj, s.skin, s.dt, 10)
+    d = pos - r["pos"]
+    d -= s.box * np.rint(d / s.box)
+    assert np.abs(d).max() <= 1e-4
+    np.testing.assert_array_equal(img, r["img"])
+    b.neighbour_update(force=True)
+    count, nbr, pos_used = b.nlist()
+    ref = oracle.nlist(s.box, pos_used, 2.8)
+    assert np.array_equal(count, ref.count)
+
+
+def test_a_layout_whose_tiles_overflow_is_refused_and_the_old_one_kept(ljmd):
+    # lj4000 at 1.7 list radii per cell edge: 3 cells a side, ~148 particles a
+    # cell, so the 27 cells around any cell hold all 4000 particles, more than
+    # a tile addresses.  The box keeps its layout and correct lists.
+    s = inputs.lj4000()
+    b = ljmd.from_system(s, "mixed_ds")
+    b.set_layout(cell_scale=1.3, order="morton")
+    with pytest.raises(ljmd.MDError) as ei:
+        b.set_layout(cell_scale=1.7, order="zrun")
+    assert "2048" in str(ei.value)
+    assert b.layout() == {"cell_scale": 1.3, "order": "morton"}
+    check_lists(b, s, 2.8)
+    f, e, w = b.force()
+    lj = _lj(s)
+    fo, eo, wo = oracle.forces(s.box, s.pos, lj)
+    S = pair_scale(s.box, s.pos, lj)
+    assert (np.linalg.norm(f - fo, axis=1) / S).max() <= 1e-5
