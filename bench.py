@@ -375,6 +375,7 @@ def bench_layouts(ljmd, s, tuning, steps=100,
     and one forced list build (binning, sort, list) timed with CUDA events."""
     import torch
     b = ljmd.from_system(s, "mixed_ds")
+    b.list_kernel = tuning.get("list_kernel", "auto")
     b.set_tuning(**{k: v for k, v in tuning.items() if k in b.TUNING})
     out = []
     for sc, od in layouts:
@@ -484,7 +485,9 @@ def run_gpu(args):
     s = inputs.fcc_system(args.ncell, seed=inputs.SEEDS["lj4m"] + rank)
     n = s.n
     box = ljmd.from_system(s, "mixed_ds")
+    box.list_kernel = args.list_kernel
     tuning = box.autotune(reps=3, cache=False)        # launch/layout autotuner
+    tuning["list_kernel"] = box.list_kernel
     thermo = torch.zeros((max(args.steps, args.warmup, 1), 1, 4), dtype=torch.float64,
                          device="cuda")
     if args.warmup:
@@ -629,6 +632,8 @@ def main():
                     help="skip the other precisions and the CPU oracle (profiling runs)")
     ap.add_argument("--layouts", action="store_true",
                     help="with --quick: still run the cell-layout A/B")
+    ap.add_argument("--list-kernel", default="auto", choices=["auto", "quads", "lanes"],
+                    help="list-build kernel (md_set_list_kernel)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

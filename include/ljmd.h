@@ -289,6 +289,27 @@ enum { MD_ORDER_ZRUN = 0, MD_ORDER_MORTON = 1 };
 md_status md_set_layout(md_box* b, double cell_scale, int32_t order);
 md_status md_get_layout(md_box* b, double* cell_scale, int32_t* order);
 
+/* List-build kernel (Sec. 3: Verlet lists from the cell decomposition; the
+ * lists are the same sets either way, decided exactly as the FP64
+ * definition |d_ij|^2 < rl^2):
+ *   MD_LIST_QUADS  one block per segment of cells, the segment's 27-cell
+ *                  neighbourhood staged in shared memory, each warp taking
+ *                  quads of particles with the candidates spread over its
+ *                  lanes (each neighbour cell narrowed to its z-run within
+ *                  reach under MD_ORDER_ZRUN)
+ *   MD_LIST_LANES  one warp per cell, one lane per particle of the cell; the
+ *                  warp stages each candidate once (dropping those beyond
+ *                  the list radius of the cell's box) and every lane tests
+ *                  it against its own particle; rows are staged in shared
+ *                  memory as 16-bit codes (K + 8 per lane, K the capacity)
+ *   MD_LIST_AUTO   (default) MD_LIST_LANES where a block's rows fit in
+ *                  96 KB of shared memory (K <= 376), else MD_LIST_QUADS
+ * MD_LIST_LANES also falls back to MD_LIST_QUADS when the rows do not fit.
+ * The setting takes effect at the next list build. */
+enum { MD_LIST_AUTO = 0, MD_LIST_QUADS = 1, MD_LIST_LANES = 2 };
+md_status md_set_list_kernel(md_box* b, int32_t kind);
+md_status md_get_list_kernel(md_box* b, int32_t* kind);
+
 /* Autotuner: times `reps` launches of the pair-force kernel for each
  * blocks-per-SM candidate, and `reps` forced list builds for each segment
  * length (automatic choice +-2) x list blocks-per-SM candidate, at the

@@ -214,12 +214,13 @@ __global__ void __launch_bounds__(LJ_FORCE_THREADS, SINGLE ? 8 : 6) k_force_f32(
             // warps of a block run ahead into the next chunk independently.
             // The warp sum is double-single (two FP32 words per partial
             // sum): FP64-class precision on the FP32 pipe, since FP64 adds
-            // are scarce on this GPU
-            const double de = 0.5 * warp_sum_ds(e), dw = 0.5 * warp_sum_ds(vir);
+            // are scarce on this GPU.  The share is stored as the (hi, lo)
+            // pair itself (pf_ds), halved exactly; the reduction converts
+            const float2 de = warp_sum_ds2(e), dw = warp_sum_ds2(vir);
             if ((threadIdx.x & 31) == 0) {
                 const size_t q = (size_t)w * LJ_FORCE_WARPS + (threadIdx.x >> 5);
-                b.part_f[2 * q] = de;
-                b.part_f[2 * q + 1] = dw;
+                reinterpret_cast<float4*>(b.part_f)[q] =
+                    make_float4(0.5f * de.x, 0.5f * de.y, 0.5f * dw.x, 0.5f * dw.y);
             }
         }
     }
@@ -612,7 +613,13 @@ __global__ void __launch_bounds__(LJ_THERMO_THREADS) k_thermo(BoxDev b, double* 
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int c = c0 + u * (int)blockDim.x + (int)threadIdx.x;
-                v[u] = c < t.z * pf ? sh[c] : make_double2(0.0, 0.0);
+                if (b.pf_ds) {   // (hi, lo) float pairs
+                    const float4 f = c < t.z * pf ? reinterpret_cast<const float4*>(b.part_f)[c]
+                                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+                    v[u] = make_double2((double)f.x + (double)f.y, (double)f.z + (double)f.w);
+                } else {
+                    v[u] = c < t.z * pf ? sh[c] : make_double2(0.0, 0.0);
+                }
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u) {

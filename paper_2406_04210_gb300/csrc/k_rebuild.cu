@@ -665,6 +665,235 @@ __global__ void __launch_bounds__(LJ_LIST_THREADS, 3) k_nlist(BoxDev b)
     if (threadIdx.x == 0 && s_longest > 0) atomicMax(&b.err[2], s_longest);   // longest list of this build
 }
 
+// ---------------------------------------------------------------------------
+// k_nlist_lanes: the same lists, one warp per cell and one lane per particle
+// of the cell.  The warp streams the candidates of the 27 neighbour cells
+// in chunks of 32: lane t loads candidate t of the chunk (coalesced, the
+// next chunk's load in flight while this one is used), adds the cell's
+// shift and drops it when its distance from the cell's box is beyond the
+// list radius (about a quarter of the 27-cell block lies there); the kept
+// candidates (shifted FP32 offset and a 16-bit code: neighbour cell k and
+// index inside it) go to a per-warp ring in shared memory.  Every 32 staged
+// candidates, each lane tests them all against its own particle -- one
+// broadcast shared-memory load per candidate for the whole cell -- and
+// appends the codes of its hits to its own row in shared memory (no
+// ballots: every lane owns its row); at the end it writes the row out as
+// list entries with 16-byte stores.  Pairs within `band` of rl^2 are
+// re-decided in FP64 as in k_nlist (checked per batch of 32: the largest
+// accepted r^2 tells whether any accepted pair lies in the band).  The x and
+// y parts of d_ij and d_ij^2 are computed as FP32 pairs.
+// ---------------------------------------------------------------------------
+constexpr int kLaneWarps = LJ_LANE_THREADS / 32;
+constexpr int kRing = 64;   // staged candidates per warp: < 32 waiting + one chunk
+
+// r^2 of the pair (i, candidate q = o_j + shift) from n = -o_i.
+__device__ __forceinline__ float lane_r2(const float2 nxy, float nz, const float4& q)
+{
+    const float2 d = __fadd2_rn(make_float2(q.x, q.y), nxy);
+    const float dz = q.z + nz;
+    const float2 s = __fmul2_rn(d, d);
+    return fmaf(dz, dz, s.x + s.y);
+}
+
+__global__ void __launch_bounds__(LJ_LANE_THREADS, 6) k_nlist_lanes(BoxDev b)
+{
+    if (!box_needs_rebuild(b)) return;
+    extern __shared__ __align__(16) uint16_t s_rows[];   // per lane: K + 8 codes
+    __shared__ __align__(16) float s_cx[kLaneWarps][kRing];   // staged candidates: o_j + shift(k),
+    __shared__ __align__(16) float s_cy[kLaneWarps][kRing];   // one array per component (pairs of
+    __shared__ __align__(16) float s_cz[kLaneWarps][kRing];   // candidates load as one 8-byte word)
+    __shared__ __align__(16) uint32_t s_cc[kLaneWarps][kRing];   // and their codes
+    __shared__ int2 s_rng[kLaneWarps][27];                // neighbour cell k: (first slot, end slot)
+    __shared__ float4 s_sh[kLaneWarps][27];               // shift(k) = (dx, dy, dz) * cell edge
+    __shared__ uint32_t s_base[kLaneWarps][32];           // entry of the first slot of cell k (27 used;
+                                                          // stale codes past a row's end index up to 31)
+    __shared__ int s_longest;
+    if (threadIdx.x == 0) s_longest = 0;
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int K = b.K;
+    uint16_t* const row = s_rows + (size_t)(warp * 32 + lane) * (K + 8);
+    uint16_t* const wend = row + K;   // codes past the capacity are counted, written here
+    float* const rx = s_cx[warp];
+    float* const ry = s_cy[warp];
+    float* const rz = s_cz[warp];
+    uint32_t* const rc = s_cc[warp];
+    const float lo2 = b.rl2f - b.band, hi2 = b.rl2f + b.band;
+    const float rcull = hi2 + 1e-3f;   // staging margin for the rounding of the shifted offsets
+    const float4* __restrict__ posq = b.posq;
+    int longest = 0;
+    const int nwarp = gridDim.x * kLaneWarps;
+    for (int gc = blockIdx.x * kLaneWarps + warp; gc < b.ncell; gc += nwarp) {
+        const int r = b.cell_rep[gc];
+        if (!rep_needs_rebuild(b, r)) continue;   // warp-uniform
+        const RepDev& R = b.rep[r];
+        int cx, cy;
+        const int cz = cell_coords(R, gc, cx, cy);
+        const int cs = b.cell_start[gc], n = b.cell_end[gc] - cs;
+        if (lane == 0 && gc == R.cell_off) atomicAdd(&b.nbuild[r], 1ull);
+        __syncwarp();
+        if (lane < 27) {
+            const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
+            const int cn = R.cell_off + wrapi(cx + dx, R.nc[0]) +
+                           R.nc[0] * (wrapi(cy + dy, R.nc[1]) + R.nc[1] * wrapi(cz + dz, R.nc[2]));
+            const int js = b.cell_start[cn], je = b.cell_end[cn];
+            s_rng[warp][lane] = make_int2(js, je);
+            s_sh[warp][lane] = make_float4((float)dx * R.ellf[0], (float)dy * R.ellf[1], (float)dz * R.ellf[2], 0.f);
+            s_base[warp][lane] = entry_make(lane, js);
+            if (je - js > LJ_TILE_MAX) atomicOr(&b.err[0], LJ_ERRBIT_TILE);   // the 11-bit index: never at LJ densities
+        }
+        __syncwarp();
+        // the cell's box: offsets from the cell centre within half an edge
+        const float hx = 0.5f * R.ellf[0], hy = 0.5f * R.ellf[1], hz = 0.5f * R.ellf[2];
+        for (int ib = 0; ib < n; ib += 32) {
+            const bool act = ib + lane < n;
+            const int i = cs + (act ? ib + lane : 0);
+            float4 pi = posq[i];
+            if (!act) pi = make_float4(1.0e30f, 1.0e30f, 1.0e30f, 0.f);   // a far point: r^2 is inf
+            const float2 nxy = make_float2(-pi.x, -pi.y);
+            const float nz = -pi.z;
+            const uint32_t self = (13u << LJ_TILE_BITS) | (uint32_t)(ib + lane);   // the particle itself
+            uint16_t* wp = row;
+            unsigned head = 0, tail = 0;   // ring positions (free-running; head stays a multiple of 32)
+            // test the staged candidates [head, head + cnt) against the lane's
+            // particle and append the hits
+            auto batch = [&](int cnt) {
+                uint16_t* const c0 = wp;
+                const int h0 = (int)(head & (kRing - 1));
+                float m = 0.f;   // largest accepted r^2 of the batch
+                if (cnt == 32 && __reduce_min_sync(0xffffffffu, K - (int)(wp - row)) >= 32) {
+                    // branch-free, two candidates per step with FP32-pair
+                    // arithmetic: every candidate's code is written to the
+                    // next free slot (32-bit shared address), which advances
+                    // only on a hit
+                    uint32_t wa = (uint32_t)__cvta_generic_to_shared(wp);
+                    const float2 px = make_float2(nxy.x, nxy.x), py = make_float2(nxy.y, nxy.y),
+                                 pz = make_float2(nz, nz);
+#pragma unroll 4
+                    for (int u = 0; u < 32; u += 2) {
+                        const float2 qx = *reinterpret_cast<const float2*>(rx + h0 + u);
+                        const float2 qy = *reinterpret_cast<const float2*>(ry + h0 + u);
+                        const float2 qz = *reinterpret_cast<const float2*>(rz + h0 + u);
+                        const uint2 cc = *reinterpret_cast<const uint2*>(rc + h0 + u);
+                        const float2 dx = __fadd2_rn(qx, px), dy = __fadd2_rn(qy, py), dz = __fadd2_rn(qz, pz);
+                        const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+                        const bool h1 = (r2.x < hi2) & (cc.x != self);
+                        asm volatile("st.shared.u16 [%0], %1;" ::"r"(wa), "h"((unsigned short)cc.x));
+                        wa += h1 ? 2u : 0u;
+                        m = fmaxf(m, h1 ? r2.x : 0.f);
+                        const bool h2 = (r2.y < hi2) & (cc.y != self);
+                        asm volatile("st.shared.u16 [%0], %1;" ::"r"(wa), "h"((unsigned short)cc.y));
+                        wa += h2 ? 2u : 0u;
+                        m = fmaxf(m, h2 ? r2.y : 0.f);
+                    }
+                    asm volatile("" ::: "memory");   // the stores above stay above
+                    __syncwarp();                      // and are seen by the reads below
+                    wp = row + ((wa - (uint32_t)__cvta_generic_to_shared(row)) >> 1);
+                } else {
+                    for (int u = 0; u < cnt; ++u) {
+                        const float4 q = make_float4(rx[h0 + u], ry[h0 + u], rz[h0 + u], 0.f);
+                        const float r2 = lane_r2(nxy, nz, q);
+                        const uint32_t code = rc[h0 + u];
+                        if (r2 < hi2 && code != self) {
+                            *(wp < wend ? wp : wend) = (uint16_t)code;
+                            ++wp;
+                            m = fmaxf(m, r2);
+                        }
+                    }
+                }
+                // FP64 decision of the batch's accepted pairs near rl (rare)
+                if (__any_sync(0xffffffffu, m >= lo2) && m >= lo2) {
+                    uint16_t* w = c0;
+                    uint16_t* const e = wp < wend ? wp : wend;
+                    for (uint16_t* q = c0; q < e; ++q) {
+                        const uint32_t code = *q;
+                        const int k = (int)(code >> LJ_TILE_BITS);
+                        const int j = (int)(s_base[warp][k] & LJ_IDX_MASK) + (int)(code & LJ_TILE_MASK);
+                        const float4 pj = posq[j];
+                        const float4 sh = s_sh[warp][k];
+                        const float4 qj = make_float4(pj.x + sh.x, pj.y + sh.y, pj.z + sh.z, 0.f);
+                        if (lane_r2(nxy, nz, qj) < lo2 || exact_within(b, R, i, j)) *w++ = (uint16_t)code;
+                    }
+                    wp = w + (wp - e);   // codes past the capacity stay counted
+                }
+                head += 32u;
+            };
+            // chunk iterator over the neighbour cells: (k, j0), 32 slots at a time
+            int k = 0, j0 = s_rng[warp][0].x;
+            while (k < 27 && j0 >= s_rng[warp][k].y) {
+                ++k;
+                if (k < 27) j0 = s_rng[warp][k].x;
+            }
+            float4 raw = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (k < 27 && j0 + lane < s_rng[warp][k].y) raw = posq[j0 + lane];
+            while (k < 27) {
+                const int kc = k, len = min(32, s_rng[warp][k].y - j0);
+                const int ic = j0 - s_rng[warp][k].x + lane;   // index of this lane's candidate in cell kc
+                const float4 cur = raw;
+                j0 += 32;
+                while (k < 27 && j0 >= s_rng[warp][k].y) {
+                    ++k;
+                    if (k < 27) j0 = s_rng[warp][k].x;
+                }
+                if (k < 27 && j0 + lane < s_rng[warp][k].y) raw = posq[j0 + lane];   // next chunk, in flight
+                // stage: shift into the cell's frame, keep what can be within reach of the cell
+                const float4 sh = s_sh[warp][kc];
+                const float qx = cur.x + sh.x, qy = cur.y + sh.y, qz = cur.z + sh.z;
+                const float gx = fmaxf(fabsf(qx) - hx, 0.f), gy = fmaxf(fabsf(qy) - hy, 0.f),
+                            gz = fmaxf(fabsf(qz) - hz, 0.f);
+                const bool keep = lane < len && fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < rcull;
+                const unsigned bal = __ballot_sync(0xffffffffu, keep);
+                if (keep) {
+                    const int t = (int)((tail + __popc(bal & lt)) & (kRing - 1));
+                    rx[t] = qx;
+                    ry[t] = qy;
+                    rz[t] = qz;
+                    rc[t] = ((uint32_t)kc << LJ_TILE_BITS) | (uint32_t)ic;
+                }
+                tail += __popc(bal);
+                __syncwarp();
+                if (tail - head >= 32) batch(32);
+                __syncwarp();
+            }
+            if (tail > head) batch((int)(tail - head));
+            __syncwarp();
+            const int c = (int)(wp - row);
+            if (act) {
+                // codes -> list entries (entry of cell k's first slot + index), 8 at a time
+                const int cst = min(c, K);
+                uint4* const dst = reinterpret_cast<uint4*>(b.nbr + (size_t)K * i);
+                const uint4* const src = reinterpret_cast<const uint4*>(row);
+                const uint32_t* const base = s_base[warp];
+                for (int e = 0; 8 * e < cst; ++e) {   // rows end inside a block: masked by the count
+                    const uint4 h = src[e];
+                    uint32_t o[8];
+                    const uint32_t hw[4] = {h.x, h.y, h.z, h.w};
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const uint32_t lo = hw[u] & 0xffffu, hi = hw[u] >> 16;
+                        o[2 * u] = base[lo >> LJ_TILE_BITS] + (lo & LJ_TILE_MASK);
+                        o[2 * u + 1] = base[hi >> LJ_TILE_BITS] + (hi & LJ_TILE_MASK);
+                    }
+                    dst[2 * e] = make_uint4(o[0], o[1], o[2], o[3]);
+                    dst[2 * e + 1] = make_uint4(o[4], o[5], o[6], o[7]);
+                }
+                b.nbr_count[i] = c;
+                if (c > K) {
+                    atomicOr(&b.err[0], LJ_ERRBIT_CAPACITY);
+                    atomicMax(&b.err[1], c);
+                }
+                longest = max(longest, c);
+            }
+            __syncwarp();
+        }
+    }
+    longest = __reduce_max_sync(0xffffffffu, longest);
+    if (lane == 0 && longest > 0) atomicMax(&s_longest, longest);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_longest > 0) atomicMax(&b.err[2], s_longest);
+}
+
 // Condition of the step graph's list-update node: 1 when the integrator (or
 // the host) raised the box-wide rebuild word, so that steps without a build
 // launch none of the rebuild kernels; each 1 is counted (launch accounting).
@@ -725,6 +954,23 @@ cudaError_t launch_nlist(const BoxDev& b, Launch l)
         attr = true;
     }
     k_nlist<<<l.grid, LJ_LIST_THREADS, dyn, l.s>>>(b);
+    return cudaGetLastError();
+}
+
+// Shared memory of k_nlist_lanes for capacity K: one row of K + 8 16-bit
+// codes per lane (rows stay 16-byte aligned).
+size_t nlist_lanes_smem(int K) { return (size_t)LJ_LANE_THREADS * (size_t)(K + 8) * 2u; }
+
+cudaError_t launch_nlist_lanes(const BoxDev& b, Launch l)
+{
+    static size_t attr = 0;
+    const size_t dyn = nlist_lanes_smem(b.K);
+    if (dyn > attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_nlist_lanes, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        if (e != cudaSuccess) return e;
+        attr = dyn;
+    }
+    k_nlist_lanes<<<l.grid, LJ_LANE_THREADS, dyn, l.s>>>(b);
     return cudaGetLastError();
 }
 

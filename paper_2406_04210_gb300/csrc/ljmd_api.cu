@@ -115,6 +115,7 @@ struct md_box {
     int min_capacity = 0;
     bool autofit = false;      // fit the capacity after the next full build
     double cell_scale = 1.0;   // cell edge / list radius (>= 1)
+    int list_kernel = 0;       // MD_LIST_AUTO / MD_LIST_QUADS / MD_LIST_LANES
     int order = 0;             // order inside a cell (MD_ORDER_*)
     int force_per_sm = 0;      // 0 = automatic (tuning)
     int list_per_sm = 0;
@@ -260,6 +261,27 @@ Launch llist(md_box* b)
     return Launch{std::max(1, std::min(b->d.nseg, b->nsm * per_sm)), LJ_LIST_THREADS, b->stream};
 }
 
+// The lane-per-particle list kernel runs where its rows (K + 4 entries per
+// lane) fit in 96 KB of shared memory per block, unless the quad kernel is
+// asked for.
+bool lanes_list(md_box* b)
+{
+    return b->list_kernel != MD_LIST_QUADS && nlist_lanes_smem(b->d.K) <= 96u * 1024u;
+}
+
+cudaError_t launch_list(md_box* b, cudaStream_t s)
+{
+    if (lanes_list(b)) {
+        const int per_sm = b->list_per_sm > 0 ? b->list_per_sm : 4;
+        const int warps = LJ_LANE_THREADS / 32;
+        return launch_nlist_lanes(
+            b->d, Launch{std::max(1, std::min((b->d.ncell + warps - 1) / warps, b->nsm * per_sm)), LJ_LANE_THREADS, s});
+    }
+    Launch l = llist(b);
+    l.s = s;
+    return launch_nlist(b->d, l);
+}
+
 // Fence: internal stream waits for the caller's stream.
 md_status enter(md_box* b)
 {
@@ -329,7 +351,7 @@ md_status enqueue_rebuild(md_box* b, int from_abs, cudaStream_t s = nullptr)
     CK(b, launch_scan_tiles(b->d, b->d_tiles, (int)b->tiles.size(), b->d_tile_sum, lt));
     CK(b, launch_scatter(b->d, l));
     CK(b, launch_sortgather(b->d, on(b->all_pairs ? lch(b) : lcell(b)), l));
-    if (!b->all_pairs) CK(b, launch_nlist(b->d, on(llist(b))));
+    if (!b->all_pairs) CK(b, launch_list(b, s));
     b->launches += rebuild_kernels(b);
     return MD_OK;
 }
@@ -777,7 +799,7 @@ md_status ckpt_copy(md_box* b, int c, bool restore)
 md_status replay_lists(md_box* b)
 {
     CKS(set_all_rebuild(b));
-    CK(b, launch_nlist(b->d, llist(b)));
+    CK(b, launch_list(b, b->stream));
     CK(b, launch_force(b->d, 0, lforce(b)));
     b->launches += 2;
     return MD_OK;
@@ -1023,6 +1045,7 @@ md_status md_batch_create(md_box** out, int32_t nrep, const int64_t* n, const do
         CKS(dev_alloc(b, &d.part_k, LJ_KIN_WARPS * std::max<size_t>(1, b->chunks.size())));
         CKS(dev_alloc(b, &d.part_f, 2 * LJ_FORCE_WARPS * std::max<size_t>(1, b->chunks.size())));
         d.pf_stride = prec == MD_PREC_FP64 ? LJ_F64_WARPS : LJ_FORCE_WARPS;
+        d.pf_ds = prec == MD_PREC_FP64 ? 0 : 1;
         CKS(dev_alloc(b, &b->d_type_user, std::max<int64_t>(1, ntot)));
         CK(b, cudaMemcpyAsync(b->d_rep, b->reps.data(), sizeof(RepDev) * b->reps.size(),
                               cudaMemcpyHostToDevice, b->stream));
@@ -1119,6 +1142,7 @@ md_status md_set_lj(md_box* b, int32_t ntypes, const double* eps, const double* 
     b->d.all_pairs = all_pairs ? 1 : 0;
     // (E_pot, W) shares per chunk: the list kernels leave one per warp
     b->d.pf_stride = all_pairs ? 1 : b->prec == MD_PREC_FP64 ? LJ_F64_WARPS : LJ_FORCE_WARPS;
+    b->d.pf_ds = (!all_pairs && b->prec != MD_PREC_FP64) ? 1 : 0;   // the FP32 list kernel's shares
     if (all_pairs && !b->d.ap_cnt) {
         // j slices per chunk: enough work items to fill the GPU, each slice
         // at least ~128 particles
@@ -1843,6 +1867,24 @@ md_status md_set_layout(md_box* b, double cell_scale, int32_t order)
     CKS(enter(b));
     CKS(set_layout(b, cell_scale, order));
     CKS(leave(b));
+    return MD_OK;
+}
+
+md_status md_set_list_kernel(md_box* b, int32_t kind)
+{
+    if (!b || kind < MD_LIST_AUTO || kind > MD_LIST_LANES)
+        return fail(b, MD_ERR_ARG, "md_set_list_kernel: kind must be 0, 1 or 2");
+    if (kind != b->list_kernel) {
+        b->list_kernel = kind;
+        invalidate_graphs(b);
+    }
+    return MD_OK;
+}
+
+md_status md_get_list_kernel(md_box* b, int32_t* kind)
+{
+    if (!b || !kind) return MD_ERR_ARG;
+    *kind = b->list_kernel;
     return MD_OK;
 }
 

@@ -47,6 +47,7 @@
 #define LJ_THERMO_THREADS 256  // threads of the energy reduction
 #define LJ_THERMO_CHUNKS 256   // chunks of one energy-reduction item
 #define LJ_LIST_THREADS 256    // threads of the list-build kernel
+#define LJ_LANE_THREADS 128    // threads of the lane-per-particle list-build kernel
 #define LJ_F64_THREADS 128     // threads of the FP64 pair kernel (one per particle)
 #define LJ_F64_WARPS (LJ_F64_THREADS / 32)   // its (E_pot, W) shares per chunk
 #define LJ_TPP 4               // threads per particle in the pair kernels
@@ -188,6 +189,8 @@ struct BoxDev {
     // per-chunk FP64 partial sums
     double* part_f;            // [(chunk*pf_stride + q)*2 + 0] = E_pot share, [+1] = W share
     int pf_stride;             // (E_pot, W) shares per chunk: one per warp of the list kernels, 1 for all pairs
+    int pf_ds;                 // 1: each share is a double-single pair (hi, lo floats in the double's
+                               // 8 bytes: the FP32 list kernel), 0: a double
     double* part_k;            // [chunk*LJ_KIN_WARPS + warp] = E_kin share
     double* part_t;            // [item*3 + 0..2] = E_pot, W, E_kin of a reduction item
     unsigned* tcount;          // per replica: reduction items finished (last one resets)
@@ -241,7 +244,7 @@ __device__ __forceinline__ void ds_from_double(double x, float& h, float& l)
 // two-sum at every step), returned as FP64 in every lane: an FP64-class sum
 // on the FP32 pipe (FP64 adds are scarce on this GPU).  The butterfly order
 // is fixed, so the result is deterministic.
-__device__ __forceinline__ double warp_sum_ds(float x)
+__device__ __forceinline__ float2 warp_sum_ds2(float x)
 {
     float h = x, l = 0.f;
 #pragma unroll
@@ -249,7 +252,12 @@ __device__ __forceinline__ double warp_sum_ds(float x)
         const float oh = __shfl_xor_sync(0xffffffffu, h, o), ol = __shfl_xor_sync(0xffffffffu, l, o);
         ds_add_ds(h, l, oh, ol);
     }
-    return (double)h + (double)l;
+    return make_float2(h, l);
+}
+__device__ __forceinline__ double warp_sum_ds(float x)
+{
+    const float2 s = warp_sum_ds2(x);
+    return (double)s.x + (double)s.y;
 }
 
 // Cheap block-level early exit of the rebuild kernels: nothing to do unless
@@ -491,6 +499,10 @@ int ljmd_scan_tile_cells();
 cudaError_t launch_scatter(const BoxDev& b, Launch l);
 cudaError_t launch_sortgather(const BoxDev& b, Launch l, Launch lg);   // rank (l), then gather (lg) unless all pairs
 cudaError_t launch_nlist(const BoxDev& b, Launch l);
+// one warp per cell, one lane per particle (rows staged in shared memory:
+// nlist_lanes_smem(K) bytes per block)
+cudaError_t launch_nlist_lanes(const BoxDev& b, Launch l);
+size_t nlist_lanes_smem(int K);
 // sets a step graph's IF-node condition from the box-wide rebuild word
 cudaError_t launch_set_rebuild_cond(cudaGraphConditionalHandle h, const BoxDev& b, unsigned long long* runs,
                                     cudaStream_t s);

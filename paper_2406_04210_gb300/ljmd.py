@@ -30,6 +30,7 @@ EXPORTS = ["md_set_allocator", "md_batch_create", "md_box_create", "md_box_destr
            "md_set_lj", "md_neighbour_update", "md_force", "md_integrate", "md_adjoint",
            "md_get_state", "md_set_state", "md_get_nlist", "md_get_info", "md_set_tuning",
            "md_get_tuning", "md_autotune", "md_set_layout", "md_get_layout",
+           "md_set_list_kernel", "md_get_list_kernel",
            "md_set_profiling", "md_get_profile", "md_pair_hist", "md_force_noalloc",
            "md_set_thermostat",
            "md_last_error", "md_status_string"]
@@ -96,6 +97,8 @@ def load(path: str | None = None):
         L.md_autotune.argtypes = [vp, i32, vp]
         L.md_set_layout.argtypes = [vp, d, i32]
         L.md_get_layout.argtypes = [vp, vp, vp]
+        L.md_set_list_kernel.argtypes = [vp, i32]
+        L.md_get_list_kernel.argtypes = [vp, vp]
         L.md_set_profiling.argtypes = [vp, i32]
         L.md_pair_hist.argtypes = [vp, i32, d, d, d, vp, vp, vp]
         L.md_force_noalloc.argtypes = [vp, vp, vp, vp]
@@ -348,6 +351,19 @@ class Box:
         sc = cur["cell_scale"] if cell_scale is None else float(cell_scale)
         od = self.ORDERS[cur["order"] if order is None else order]
         self._check(self._lib.md_set_layout(self._h, sc, od), "md_set_layout")
+
+    LIST_KERNELS = {"auto": 0, "quads": 1, "lanes": 2}
+
+    @property
+    def list_kernel(self):
+        """List-build kernel: "auto", "quads" or "lanes" (md_set_list_kernel)."""
+        k = ctypes.c_int32()
+        self._check(self._lib.md_get_list_kernel(self._h, ctypes.byref(k)), "md_get_list_kernel")
+        return {v: n for n, v in self.LIST_KERNELS.items()}[k.value]
+
+    @list_kernel.setter
+    def list_kernel(self, kind):
+        self._check(self._lib.md_set_list_kernel(self._h, self.LIST_KERNELS[kind]), "md_set_list_kernel")
 
     def autotune(self, reps=5, cache=True):
         """Measure and apply the fastest launch/layout settings (md_autotune).

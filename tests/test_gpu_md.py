@@ -319,9 +319,11 @@ def test_cell_layouts_keep_lists_forces_and_trajectories(ljmd, scale, order):
 def test_a_layout_whose_tiles_overflow_is_refused_and_the_old_one_kept(ljmd):
     # lj4000 at 1.7 list radii per cell edge: 3 cells a side, ~148 particles a
     # cell, so the 27 cells around any cell hold all 4000 particles, more than
-    # a tile addresses.  The box keeps its layout and correct lists.
+    # the quad kernel's tile addresses.  The box keeps its layout and correct
+    # lists.  (The lane kernel has no tile: there the layout is accepted.)
     s = inputs.lj4000()
     b = ljmd.from_system(s, "mixed_ds")
+    b.list_kernel = "quads"
     b.set_layout(cell_scale=1.3, order="morton")
     with pytest.raises(ljmd.MDError) as ei:
         b.set_layout(cell_scale=1.7, order="zrun")
@@ -333,3 +335,41 @@ def test_a_layout_whose_tiles_overflow_is_refused_and_the_old_one_kept(ljmd):
     fo, eo, wo = oracle.forces(s.box, s.pos, lj)
     S = pair_scale(s.box, s.pos, lj)
     assert (np.linalg.norm(f - fo, axis=1) / S).max() <= 1e-5
+
+
+@pytest.mark.parametrize("kind", ["quads", "lanes"])
+@pytest.mark.parametrize("case", ["lj4000", "binary3000", "lj4000_big_cells", "fcc2048_regrow", "lj4000_3_cells"])
+def test_both_list_kernels_build_the_fp64_lists(ljmd, kind, case):
+    # the quad kernel (candidates over lanes) and the lane kernel (particles
+    # over lanes) build the same sets, equal to the FP64 definition; big
+    # cells (62 particles a cell) take the lane kernel's two-pass path, and a
+    # capacity of 16 makes both overflow and regrow
+    if case == "binary3000":
+        s = inputs.binary_random_system(n=3000, seed=17)
+        s.pos = oracle.fire(s.box, s.pos, _lj(s), s.type, maxit=300, ftol=1e-2)[0]
+    elif case == "fcc2048_regrow":
+        s = inputs.fcc_system(8, seed=3)
+    else:
+        s = inputs.lj4000()
+    b = ljmd.from_system(s, "mixed_ds")
+    b.list_kernel = kind
+    assert b.list_kernel == kind
+    if case == "lj4000_big_cells":
+        b.set_layout(cell_scale=1.3)
+    if case == "lj4000_3_cells":
+        # 148 particles a cell: five passes of 32 lanes per cell; beyond the
+        # quad kernel's tile
+        if kind == "quads":
+            pytest.skip("a 27-cell tile over 2048 particles: refused by the quad kernel")
+        b.set_layout(cell_scale=1.7)
+    if case == "fcc2048_regrow":
+        b.set_tuning(capacity=16)
+    b.neighbour_update(force=True)
+    rl = float(np.max(s.rcut)) + s.skin
+    check_lists(b, s, rl)
+    f, e, w = b.force()
+    lj = _lj(s)
+    fo, eo, wo = oracle.forces(s.box, s.pos, lj, s.type)
+    S = pair_scale(s.box, s.pos, lj, s.type)
+    assert (np.linalg.norm(f - fo, axis=1) / S).max() <= 1e-5
+    assert abs(e[0] - eo) <= 1e-5 * abs(eo)
