@@ -310,6 +310,16 @@ enum { MD_LIST_AUTO = 0, MD_LIST_QUADS = 1, MD_LIST_LANES = 2 };
 md_status md_set_list_kernel(md_box* b, int32_t kind);
 md_status md_get_list_kernel(md_box* b, int32_t* kind);
 
+/* Step graphs: with on = 1 (default) the list update of each captured step
+ * is a conditional (IF) node, so steps without a list build launch one tiny
+ * kernel; with on = 0 the rebuild kernels are captured unconditionally and
+ * exit early when no build is due (same results; for profilers that cannot
+ * look inside graphs with conditional nodes).  If the runtime refuses the
+ * conditional node the box falls back to on = 0 by itself; md_get_graph_
+ * conditional reads the mode in use. */
+md_status md_set_graph_conditional(md_box* b, int32_t on);
+md_status md_get_graph_conditional(md_box* b, int32_t* on);
+
 /* Autotuner: times `reps` launches of the pair-force kernel for each
  * blocks-per-SM candidate, and `reps` forced list builds for each segment
  * length (automatic choice +-2) x list blocks-per-SM candidate, at the

@@ -698,7 +698,9 @@ __device__ __forceinline__ float lane_r2(const float2 nxy, float nz, const float
 __global__ void __launch_bounds__(LJ_LANE_THREADS, 6) k_nlist_lanes(BoxDev b)
 {
     if (!box_needs_rebuild(b)) return;
-    extern __shared__ __align__(16) uint16_t s_rows[];   // per lane: K + 8 codes
+    // rows, slot-major per warp: code e of lane l at [e][l] (the 32 lanes'
+    // stores of one step fall in distinct banks whatever their counts)
+    extern __shared__ __align__(16) uint16_t s_rows[];   // per warp: (K + 8) x 32 codes
     __shared__ __align__(16) float s_cx[kLaneWarps][kRing];   // staged candidates: o_j + shift(k),
     __shared__ __align__(16) float s_cy[kLaneWarps][kRing];   // one array per component (pairs of
     __shared__ __align__(16) float s_cz[kLaneWarps][kRing];   // candidates load as one 8-byte word)
@@ -713,8 +715,8 @@ __global__ void __launch_bounds__(LJ_LANE_THREADS, 6) k_nlist_lanes(BoxDev b)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const int K = b.K;
-    uint16_t* const row = s_rows + (size_t)(warp * 32 + lane) * (K + 8);
-    uint16_t* const wend = row + K;   // codes past the capacity are counted, written here
+    uint16_t* const row = s_rows + (size_t)warp * (K + 8) * 32 + lane;   // slot e at row[32 e]
+    // codes past the capacity are counted, written at slot K
     float* const rx = s_cx[warp];
     float* const ry = s_cy[warp];
     float* const rz = s_cz[warp];
@@ -754,20 +756,20 @@ __global__ void __launch_bounds__(LJ_LANE_THREADS, 6) k_nlist_lanes(BoxDev b)
             const float2 nxy = make_float2(-pi.x, -pi.y);
             const float nz = -pi.z;
             const uint32_t self = (13u << LJ_TILE_BITS) | (uint32_t)(ib + lane);   // the particle itself
-            uint16_t* wp = row;
+            int cnt = 0;                   // codes appended (slots filled, up to K)
             unsigned head = 0, tail = 0;   // ring positions (free-running; head stays a multiple of 32)
             // test the staged candidates [head, head + cnt) against the lane's
             // particle and append the hits
-            auto batch = [&](int cnt) {
-                uint16_t* const c0 = wp;
+            auto batch = [&](int nb) {
+                const int c0 = cnt;
                 const int h0 = (int)(head & (kRing - 1));
                 float m = 0.f;   // largest accepted r^2 of the batch
-                if (cnt == 32 && __reduce_min_sync(0xffffffffu, K - (int)(wp - row)) >= 32) {
+                if (nb == 32 && __reduce_min_sync(0xffffffffu, K - cnt) >= 32) {
                     // branch-free, two candidates per step with FP32-pair
                     // arithmetic: every candidate's code is written to the
                     // next free slot (32-bit shared address), which advances
                     // only on a hit
-                    uint32_t wa = (uint32_t)__cvta_generic_to_shared(wp);
+                    uint32_t wa = (uint32_t)__cvta_generic_to_shared(row + 32 * cnt);
                     const float2 px = make_float2(nxy.x, nxy.x), py = make_float2(nxy.y, nxy.y),
                                  pz = make_float2(nz, nz);
 #pragma unroll 4
@@ -780,42 +782,42 @@ __global__ void __launch_bounds__(LJ_LANE_THREADS, 6) k_nlist_lanes(BoxDev b)
                         const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
                         const bool h1 = (r2.x < hi2) & (cc.x != self);
                         asm volatile("st.shared.u16 [%0], %1;" ::"r"(wa), "h"((unsigned short)cc.x));
-                        wa += h1 ? 2u : 0u;
+                        wa += h1 ? 64u : 0u;
                         m = fmaxf(m, h1 ? r2.x : 0.f);
                         const bool h2 = (r2.y < hi2) & (cc.y != self);
                         asm volatile("st.shared.u16 [%0], %1;" ::"r"(wa), "h"((unsigned short)cc.y));
-                        wa += h2 ? 2u : 0u;
+                        wa += h2 ? 64u : 0u;
                         m = fmaxf(m, h2 ? r2.y : 0.f);
                     }
                     asm volatile("" ::: "memory");   // the stores above stay above
                     __syncwarp();                      // and are seen by the reads below
-                    wp = row + ((wa - (uint32_t)__cvta_generic_to_shared(row)) >> 1);
+                    cnt = (int)((wa - (uint32_t)__cvta_generic_to_shared(row)) >> 6);
                 } else {
-                    for (int u = 0; u < cnt; ++u) {
+                    for (int u = 0; u < nb; ++u) {
                         const float4 q = make_float4(rx[h0 + u], ry[h0 + u], rz[h0 + u], 0.f);
                         const float r2 = lane_r2(nxy, nz, q);
                         const uint32_t code = rc[h0 + u];
                         if (r2 < hi2 && code != self) {
-                            *(wp < wend ? wp : wend) = (uint16_t)code;
-                            ++wp;
+                            row[32 * min(cnt, K)] = (uint16_t)code;
+                            ++cnt;
                             m = fmaxf(m, r2);
                         }
                     }
                 }
                 // FP64 decision of the batch's accepted pairs near rl (rare)
                 if (__any_sync(0xffffffffu, m >= lo2) && m >= lo2) {
-                    uint16_t* w = c0;
-                    uint16_t* const e = wp < wend ? wp : wend;
-                    for (uint16_t* q = c0; q < e; ++q) {
-                        const uint32_t code = *q;
+                    int w = c0;
+                    const int e = min(cnt, K);
+                    for (int q = c0; q < e; ++q) {
+                        const uint32_t code = row[32 * q];
                         const int k = (int)(code >> LJ_TILE_BITS);
                         const int j = (int)(s_base[warp][k] & LJ_IDX_MASK) + (int)(code & LJ_TILE_MASK);
                         const float4 pj = posq[j];
                         const float4 sh = s_sh[warp][k];
                         const float4 qj = make_float4(pj.x + sh.x, pj.y + sh.y, pj.z + sh.z, 0.f);
-                        if (lane_r2(nxy, nz, qj) < lo2 || exact_within(b, R, i, j)) *w++ = (uint16_t)code;
+                        if (lane_r2(nxy, nz, qj) < lo2 || exact_within(b, R, i, j)) row[32 * w++] = (uint16_t)code;
                     }
-                    wp = w + (wp - e);   // codes past the capacity stay counted
+                    cnt = w + (cnt - e);   // codes past the capacity stay counted
                 }
                 head += 32u;
             };
@@ -858,25 +860,20 @@ __global__ void __launch_bounds__(LJ_LANE_THREADS, 6) k_nlist_lanes(BoxDev b)
             }
             if (tail > head) batch((int)(tail - head));
             __syncwarp();
-            const int c = (int)(wp - row);
+            const int c = cnt;
             if (act) {
-                // codes -> list entries (entry of cell k's first slot + index), 8 at a time
+                // codes -> list entries (entry of cell k's first slot + index), 4 at a time
                 const int cst = min(c, K);
                 uint4* const dst = reinterpret_cast<uint4*>(b.nbr + (size_t)K * i);
-                const uint4* const src = reinterpret_cast<const uint4*>(row);
                 const uint32_t* const base = s_base[warp];
-                for (int e = 0; 8 * e < cst; ++e) {   // rows end inside a block: masked by the count
-                    const uint4 h = src[e];
-                    uint32_t o[8];
-                    const uint32_t hw[4] = {h.x, h.y, h.z, h.w};
+                for (int e = 0; 4 * e < cst; ++e) {   // rows end inside a block: masked by the count
+                    uint32_t o[4];
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        const uint32_t lo = hw[u] & 0xffffu, hi = hw[u] >> 16;
-                        o[2 * u] = base[lo >> LJ_TILE_BITS] + (lo & LJ_TILE_MASK);
-                        o[2 * u + 1] = base[hi >> LJ_TILE_BITS] + (hi & LJ_TILE_MASK);
+                        const uint32_t h = row[32 * (4 * e + u)];
+                        o[u] = base[h >> LJ_TILE_BITS] + (h & LJ_TILE_MASK);
                     }
-                    dst[2 * e] = make_uint4(o[0], o[1], o[2], o[3]);
-                    dst[2 * e + 1] = make_uint4(o[4], o[5], o[6], o[7]);
+                    dst[e] = make_uint4(o[0], o[1], o[2], o[3]);
                 }
                 b.nbr_count[i] = c;
                 if (c > K) {
@@ -957,8 +954,8 @@ cudaError_t launch_nlist(const BoxDev& b, Launch l)
     return cudaGetLastError();
 }
 
-// Shared memory of k_nlist_lanes for capacity K: one row of K + 8 16-bit
-// codes per lane (rows stay 16-byte aligned).
+// Shared memory of k_nlist_lanes for capacity K: K + 8 16-bit code slots
+// per lane (slot K takes the codes past the capacity).
 size_t nlist_lanes_smem(int K) { return (size_t)LJ_LANE_THREADS * (size_t)(K + 8) * 2u; }
 
 cudaError_t launch_nlist_lanes(const BoxDev& b, Launch l)

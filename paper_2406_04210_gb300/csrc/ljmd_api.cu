@@ -1881,6 +1881,23 @@ md_status md_set_list_kernel(md_box* b, int32_t kind)
     return MD_OK;
 }
 
+md_status md_set_graph_conditional(md_box* b, int32_t on)
+{
+    if (!b || on < 0 || on > 1) return fail(b, MD_ERR_ARG, "md_set_graph_conditional: on must be 0 or 1");
+    if ((on != 0) != b->use_cond) {
+        b->use_cond = on != 0;
+        invalidate_graphs(b);
+    }
+    return MD_OK;
+}
+
+md_status md_get_graph_conditional(md_box* b, int32_t* on)
+{
+    if (!b || !on) return MD_ERR_ARG;
+    *on = b->use_cond ? 1 : 0;
+    return MD_OK;
+}
+
 md_status md_get_list_kernel(md_box* b, int32_t* kind)
 {
     if (!b || !kind) return MD_ERR_ARG;

@@ -30,7 +30,8 @@ EXPORTS = ["md_set_allocator", "md_batch_create", "md_box_create", "md_box_destr
            "md_set_lj", "md_neighbour_update", "md_force", "md_integrate", "md_adjoint",
            "md_get_state", "md_set_state", "md_get_nlist", "md_get_info", "md_set_tuning",
            "md_get_tuning", "md_autotune", "md_set_layout", "md_get_layout",
-           "md_set_list_kernel", "md_get_list_kernel",
+           "md_set_list_kernel", "md_get_list_kernel", "md_set_graph_conditional",
+           "md_get_graph_conditional",
            "md_set_profiling", "md_get_profile", "md_pair_hist", "md_force_noalloc",
            "md_set_thermostat",
            "md_last_error", "md_status_string"]
@@ -99,6 +100,8 @@ def load(path: str | None = None):
         L.md_get_layout.argtypes = [vp, vp, vp]
         L.md_set_list_kernel.argtypes = [vp, i32]
         L.md_get_list_kernel.argtypes = [vp, vp]
+        L.md_set_graph_conditional.argtypes = [vp, i32]
+        L.md_get_graph_conditional.argtypes = [vp, vp]
         L.md_set_profiling.argtypes = [vp, i32]
         L.md_pair_hist.argtypes = [vp, i32, d, d, d, vp, vp, vp]
         L.md_force_noalloc.argtypes = [vp, vp, vp, vp]
@@ -364,6 +367,18 @@ class Box:
     @list_kernel.setter
     def list_kernel(self, kind):
         self._check(self._lib.md_set_list_kernel(self._h, self.LIST_KERNELS[kind]), "md_set_list_kernel")
+
+    @property
+    def graph_conditional(self):
+        """True when step graphs hold the list update as a conditional node
+        (md_set_graph_conditional)."""
+        k = ctypes.c_int32()
+        self._check(self._lib.md_get_graph_conditional(self._h, ctypes.byref(k)), "md_get_graph_conditional")
+        return bool(k.value)
+
+    @graph_conditional.setter
+    def graph_conditional(self, on):
+        self._check(self._lib.md_set_graph_conditional(self._h, 1 if on else 0), "md_set_graph_conditional")
 
     def autotune(self, reps=5, cache=True):
         """Measure and apply the fastest launch/layout settings (md_autotune).

@@ -235,6 +235,24 @@ def test_deterministic(ljmd):
     np.testing.assert_array_equal(out[0][1], out[1][1])
 
 
+def test_conditional_and_plain_step_graphs_agree(ljmd):
+    # the list update as a conditional graph node (default) or as kernels that
+    # exit early: the same trajectory bit for bit, fewer launches with the node
+    s = inputs.lj4000()
+    out = []
+    for cond in (True, False):
+        b = ljmd.from_system(s, "mixed_ds")
+        b.graph_conditional = cond
+        assert b.graph_conditional == cond
+        l0 = b.info().launches
+        th = b.integrate(s.dt, 50)
+        out.append((b.get_state()[0], th, b.info().launches - l0, b.info().rebuilds))
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+    assert out[0][3] == out[1][3] >= 1
+    assert out[0][2] < out[1][2]
+
+
 def test_set_state_roundtrip(ljmd):
     s = inputs.lj4000()
     b = ljmd.from_system(s, "mixed_fp64")
