@@ -149,13 +149,15 @@ __global__ void __launch_bounds__(LJ_FORCE_THREADS, SINGLE ? 8 : 6) k_force_f32(
             const bool act = p < ch.z;
             float4 pi = make_float4(0.f, 0.f, 0.f, 0.f);
             int cnt = 0;
+            const uint4* L = reinterpret_cast<const uint4*>(b.nbr + (size_t)K * p) + l8;
+            uint4 cur = make_uint4(0u, 0u, 0u, 0u);
             if (act) {
                 pi = posq[p];
                 cnt = min(b.nbr_count[p], K);
+                cur = __ldcs(L);   // the row's first block (K >= 16 slots), in flight with the count
             }
             const int nblk = (cnt + LJ_ROW_BLOCK - 1) / LJ_ROW_BLOCK;
             const int ti = __float_as_int(pi.w);
-            const uint4* L = reinterpret_cast<const uint4*>(b.nbr + (size_t)K * p) + l8;
             float fx = 0.f, fy = 0.f, fz = 0.f, fx2 = 0.f, fy2 = 0.f, fz2 = 0.f;
             // the second pair chain: independent partial forces, or (SINGLE,
             // registers for occupancy) the first chain itself
@@ -178,7 +180,6 @@ __global__ void __launch_bounds__(LJ_FORCE_THREADS, SINGLE ? 8 : 6) k_force_f32(
                                        gx, gy, gz, e, vir);
             };
             if (nblk > 0) {
-                uint4 cur = __ldcs(L);
                 for (int blk = 1; blk < nblk; ++blk) {
                     const uint4 nxt = __ldcs(L + blk * LJ_TPP);   // in flight during this block
                     block4(cur);
