@@ -310,13 +310,15 @@ enum { MD_LIST_AUTO = 0, MD_LIST_QUADS = 1, MD_LIST_LANES = 2 };
 md_status md_set_list_kernel(md_box* b, int32_t kind);
 md_status md_get_list_kernel(md_box* b, int32_t* kind);
 
-/* Step graphs: with on = 1 (default) the list update of each captured step
- * is a conditional (IF) node, so steps without a list build launch one tiny
- * kernel; with on = 0 the rebuild kernels are captured unconditionally and
- * exit early when no build is due (same results; for profilers that cannot
- * look inside graphs with conditional nodes).  If the runtime refuses the
- * conditional node the box falls back to on = 0 by itself; md_get_graph_
- * conditional reads the mode in use. */
+/* Step graphs: with on = 1 the list update of each captured step is a
+ * conditional (IF) node, so steps without a list build launch one tiny kernel
+ * instead of the rebuild sequence; with on = 0 (default) the rebuild kernels
+ * are captured unconditionally and exit early when no build is due.  Results
+ * are the same bit for bit.  On GB300 the node costs ~4.5 us per step more
+ * than the early exits (measured at N = 2,000 and 97,556), so it pays only
+ * in launch count.  Profilers cannot look inside graphs with conditional
+ * nodes.  If the runtime refuses the node the box falls back to on = 0 by
+ * itself; md_get_graph_conditional reads the mode in use. */
 md_status md_set_graph_conditional(md_box* b, int32_t on);
 md_status md_get_graph_conditional(md_box* b, int32_t* on);
 

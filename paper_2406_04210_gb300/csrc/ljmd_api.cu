@@ -63,7 +63,7 @@ struct md_box {
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // the rebuild sequence as the body of a conditional (IF) graph node
-    bool use_cond = true;
+    bool use_cond = false;   // list update as a conditional graph node (md_set_graph_conditional)
     cudaStream_t cstream = nullptr;            // captures the node's body
     unsigned long long* d_cond_runs = nullptr; // true conditions so far (device)
     unsigned long long cond_runs_seen = 0;
