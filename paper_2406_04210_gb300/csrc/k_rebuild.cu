@@ -57,9 +57,53 @@ __device__ __forceinline__ double load_off(const BoxDev& b, int c, int p)
 }
 
 // ---------------------------------------------------------------------------
-// k_bin: wrapped FP64 position of every particle of a rebuilding replica,
-// its new cell, and the old-order copies used by the gather.
+// k_bin: new cell of every particle of a rebuilding replica, its offset from
+// the new cell's centre (offB, the state's layout), its wrapped FP64 position
+// (xabsB, the positions the lists are decided for) and the old-order copies
+// used by the gather.
+//
+// Steady state (double-single state, positions held as cell + offset): the
+// move to a neighbour cell is read off the FP32 offset (|o| >= half an edge)
+// and the new offset is o - d * edge in double-single arithmetic, so the
+// only FP64 work is forming the position x = centre + o.  A particle that
+// crosses the box, moves more than one cell, or sits in a boundary cell with
+// x outside [0, L) at FP64 rounding, takes the FP64 path of a build from
+// positions: wrap x into [0, L), cell = floor(x / edge), offset = x - centre.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ void bin_from_x(const BoxDev& b, const RepDev& R, double* x, int* im, int* q)
+{
+    for (int c = 0; c < 3; ++c) {
+        const double L = R.L[c];
+        // floor(x / L); the FP64 division (slow on this GPU) only where
+        // the quotient can round to 1 or more, or x is negative
+        const double f = (x[c] >= 0.0 && x[c] < R.wrap_hi[c]) ? 0.0 : floor(x[c] / L);
+        if (f != 0.0) {
+            x[c] = x[c] - L * f;
+            im[c] += (int)f;
+        }
+        const int qc = (int)(x[c] * R.inv_ell[c]);
+        q[c] = qc < 0 ? 0 : (qc >= R.nc[c] ? R.nc[c] - 1 : qc);
+    }
+}
+
+// offset of x from the centre of cell q, in the state's layout (the centre
+// rounded on its own, no FMA with the subtraction)
+__device__ __forceinline__ void store_offB(const BoxDev& b, const RepDev& R, int p, const double* x, const int* q)
+{
+    for (int c = 0; c < 3; ++c) {
+        const double o = x[c] - __dmul_rn((double)q[c] + 0.5, R.ell[c]);
+        if (b.prec == 0) {
+            float h, l;
+            ds_from_double(o, h, l);
+            float* ob = reinterpret_cast<float*>(b.offB);
+            ob[c * b.np + p] = h;
+            ob[3 * b.np + c * b.np + p] = l;
+        } else {
+            b.offB[c * b.np + p] = o;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(LJ_CHUNK) k_bin(BoxDev b, int from_abs)
 {
     if (!box_needs_rebuild(b)) return;
@@ -72,34 +116,52 @@ __global__ void __launch_bounds__(LJ_CHUNK) k_bin(BoxDev b, int from_abs)
         if (!act) p = ch.y;
         const RepDev& R = b.rep[r];
         double x[3];
-        int im[3];
+        int im[3], q[3];
+        for (int c = 0; c < 3; ++c) im[c] = b.img[c * b.np + p];
         if (from_abs) {
-            for (int c = 0; c < 3; ++c) {
-                x[c] = b.xabs[c * b.np + p];
-                im[c] = b.img[c * b.np + p];
-            }
+            for (int c = 0; c < 3; ++c) x[c] = b.xabs[c * b.np + p];
+            bin_from_x(b, R, x, im, q);
+            if (act) store_offB(b, R, p, x, q);
         } else {
             int cx, cy;
-            int cz = cell_coords(R, b.cell[p], cx, cy);
-            int cc[3] = {cx, cy, cz};
+            const int cz = cell_coords(R, b.cell[p], cx, cy);
+            const int cc[3] = {cx, cy, cz};
+            bool slow = b.prec != 0;
+            float nh[3], nl[3];
             for (int c = 0; c < 3; ++c) {
-                double centre = ((double)cc[c] + 0.5) * R.ell[c];
-                x[c] = centre + load_off(b, c, p);
-                im[c] = b.img[c * b.np + p];
+                double o;
+                if (b.prec == 0) {
+                    const float* s = reinterpret_cast<const float*>(b.off);
+                    const float h = s[c * b.np + p], l = s[3 * b.np + c * b.np + p];
+                    o = (double)h + (double)l;
+                    // the neighbour cell the FP32 offset lies in (at most one away)
+                    const float hh = 0.5f * R.ellf[c];
+                    const int d = h >= hh ? 1 : (h < -hh ? -1 : 0);
+                    const int qc = cc[c] + d;
+                    slow = slow || fabsf(h) >= 3.f * hh || qc < 0 || qc >= R.nc[c];
+                    q[c] = qc;
+                    // o - d * edge, double-single (d * ellf is exact)
+                    float sh = h, sl = l;
+                    ds_add_ds(sh, sl, -(float)d * R.ellf[c], -(float)d * R.ell_lo[c]);
+                    nh[c] = sh;
+                    nl[c] = sl;
+                } else {
+                    o = b.off[c * b.np + p];
+                }
+                x[c] = __dmul_rn((double)cc[c] + 0.5, R.ell[c]) + o;
+                // a boundary cell: the position must still be inside [0, L)
+                if ((cc[c] == 0 || cc[c] == R.nc[c] - 1) && !(x[c] >= 0.0 && x[c] < R.wrap_hi[c])) slow = true;
             }
-        }
-        int q[3];
-        for (int c = 0; c < 3; ++c) {
-            double L = R.L[c];
-            // floor(x / L); the FP64 division (slow on this GPU) only where
-            // the quotient can round to 1 or more, or x is negative
-            double f = (x[c] >= 0.0 && x[c] < R.wrap_hi[c]) ? 0.0 : floor(x[c] / L);
-            if (f != 0.0) {
-                x[c] = x[c] - L * f;
-                im[c] += (int)f;
+            if (slow) {
+                bin_from_x(b, R, x, im, q);
+                if (act) store_offB(b, R, p, x, q);
+            } else if (act) {
+                float* ob = reinterpret_cast<float*>(b.offB);
+                for (int c = 0; c < 3; ++c) {
+                    ob[c * b.np + p] = nh[c];
+                    ob[3 * b.np + c * b.np + p] = nl[c];
+                }
             }
-            int qc = (int)(x[c] * R.inv_ell[c]);
-            q[c] = qc < 0 ? 0 : (qc >= R.nc[c] ? R.nc[c] - 1 : qc);
         }
         int gc = R.cell_off + q[0] + R.nc[0] * (q[1] + R.nc[1] * q[2]);
         if (act)
@@ -237,13 +299,20 @@ __global__ void __launch_bounds__(LJ_CHUNK) k_scatter(BoxDev b)
 // over its 4 x 4 x 4 sub-cells first (Sec. 3: particles are sorted for
 // locality); the list build then takes whole neighbour cells.  The ranks are
 // written as each member's final slot (dst); k_gather then
-// moves the state into the sorted arrays, one thread per particle, and
-// derives the cell-relative offsets and their FP32 copy.  (All pairs: one
-// cell per replica, no order; k_sortgather gathers directly.)
+// moves the state, the new cell-relative offsets (computed by k_bin) and
+// their FP32 copy into the sorted arrays, one thread per particle.  (All
+// pairs: one cell per replica, no order; k_sortgather gathers directly.)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ unsigned long long sort_key(const BoxDev& b, const RepDev& R, int p, const double* centre)
+// FP32 offset from the new cell centre, as posq will hold it (offB, from k_bin)
+__device__ __forceinline__ float offB32(const BoxDev& b, int c, int p)
 {
-    const float z = __double2float_rn(b.xabsB[2 * b.np + p] - centre[2]);
+    if (b.prec == 0) return reinterpret_cast<const float*>(b.offB)[c * b.np + p];
+    return __double2float_rn(b.offB[c * b.np + p]);
+}
+
+__device__ __forceinline__ unsigned long long sort_key(const BoxDev& b, const RepDev& R, int p)
+{
+    const float z = offB32(b, 2, p);
     const unsigned u = __float_as_uint(z);
     const unsigned ord = (u & 0x80000000u) ? ~u : (u | 0x80000000u);   // order-preserving
     if (b.order == 0) return ((unsigned long long)ord << 32) | (unsigned)b.uidB[p];
@@ -253,32 +322,30 @@ __device__ __forceinline__ unsigned long long sort_key(const BoxDev& b, const Re
     unsigned m = 0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const double o = b.xabsB[c * b.np + p] - centre[c];
-        int sc = (int)floor((o * R.inv_ell[c] + 0.5) * 4.0);
+        int sc = (int)floorf((offB32(b, c, p) / R.ellf[c] + 0.5f) * 4.f);
         sc = sc < 0 ? 0 : (sc > 3 ? 3 : sc);
         m |= (unsigned)(sc & 1) << c | (unsigned)(sc >> 1) << (c + 3);
     }
     return ((unsigned long long)m << 58) | ((unsigned long long)ord << 26) | (unsigned)b.uidB[p];
 }
 
-// Gather particle p (old order) into slot q of cell gc, with the cell-
-// relative offsets and their FP32 copy.
-__device__ __forceinline__ void gather_one(const BoxDev& b, int p, int q, int gc, const double* centre)
+// Gather particle p (old order) into slot q of cell gc: its state, its new
+// offsets (from k_bin) and their FP32 copy.  No arithmetic.
+__device__ __forceinline__ void gather_one(const BoxDev& b, int p, int q, int gc)
 {
     int ty = b.typeB[p];
     float of[3];
     for (int c = 0; c < 3; ++c) {
-        double x = b.xabsB[c * b.np + p];
-        b.xabs[c * b.np + q] = x;
-        double o = x - centre[c];
+        b.xabs[c * b.np + q] = b.xabsB[c * b.np + p];
         if (b.prec == 0) {
-            float h, l;
-            ds_from_double(o, h, l);
+            const float* ob = reinterpret_cast<const float*>(b.offB);
             float* ofs = reinterpret_cast<float*>(b.off);
+            const float h = ob[c * b.np + p];
             ofs[c * b.np + q] = h;
-            ofs[3 * b.np + c * b.np + q] = l;
+            ofs[3 * b.np + c * b.np + q] = ob[3 * b.np + c * b.np + p];
             of[c] = h;
         } else {
+            const double o = b.offB[c * b.np + p];
             b.off[c * b.np + q] = o;
             of[c] = __double2float_rn(o);
         }
@@ -306,8 +373,7 @@ __global__ void __launch_bounds__(256) k_sortgather(BoxDev b)
             for (int s = ch.y + (int)threadIdx.x; s < ch.z; s += blockDim.x) {
                 if (s == R.p_off) atomicAdd(&b.nbuild[ch.x], 1ull);   // a re-binning
                 const int p = b.perm[s];
-                const double centre[3] = {0.5 * R.ell[0], 0.5 * R.ell[1], 0.5 * R.ell[2]};
-                gather_one(b, p, R.p_off + (b.uidB[p] - R.u_off), R.cell_off, centre);
+                gather_one(b, p, R.p_off + (b.uidB[p] - R.u_off), R.cell_off);
             }
         }
         return;
@@ -320,19 +386,15 @@ __global__ void __launch_bounds__(256) k_sortgather(BoxDev b)
         const RepDev& R = b.rep[r];
         int s0 = b.cell_start[gc];
         int n = b.cell_end[gc] - s0;
-        int cx, cy;
-        int cz = cell_coords(R, gc, cx, cy);
-        double centre[3] = {((double)cx + 0.5) * R.ell[0], ((double)cy + 0.5) * R.ell[1],
-                            ((double)cz + 0.5) * R.ell[2]};
         for (int base = 0; base < n; base += 32) {
             int idx = base + lane;
             int p = idx < n ? b.perm[s0 + idx] : -1;
             const unsigned long long none = ~0ull;
-            unsigned long long key = idx < n ? sort_key(b, R, p, centre) : none;
+            unsigned long long key = idx < n ? sort_key(b, R, p) : none;
             int rank = 0;
             for (int b2 = 0; b2 < n; b2 += 32) {
                 unsigned long long k2 =
-                    b2 == base ? key : ((b2 + lane < n) ? sort_key(b, R, b.perm[s0 + b2 + lane], centre) : none);
+                    b2 == base ? key : ((b2 + lane < n) ? sort_key(b, R, b.perm[s0 + b2 + lane]) : none);
 #pragma unroll 8
                 for (int t = 0; t < 32; ++t) {
                     unsigned long long kt = __shfl_sync(0xffffffffu, k2, t);
@@ -352,16 +414,8 @@ __global__ void __launch_bounds__(LJ_CHUNK) k_gather(BoxDev b)
         if (!rep_needs_rebuild(b, ch.x)) continue;   // block-uniform
         const int s = ch.y + (int)threadIdx.x;
         if (s >= ch.z) continue;
-        const RepDev& R = b.rep[ch.x];
         const int p = b.perm[s];
-        const int gc = b.cellB[p];
-        int cx, cy;
-        const int cz = cell_coords(R, gc, cx, cy);
-        // the centre rounded on its own (no FMA with the offset's subtraction),
-        // as the ranking kernel computes it
-        const double centre[3] = {__dmul_rn((double)cx + 0.5, R.ell[0]), __dmul_rn((double)cy + 0.5, R.ell[1]),
-                                  __dmul_rn((double)cz + 0.5, R.ell[2])};
-        gather_one(b, p, b.dst[s], gc, centre);
+        gather_one(b, p, b.dst[s], b.cellB[p]);
     }
 }
 

@@ -489,6 +489,7 @@ md_status make_grid(md_box* b)
             R.ell[c] = R.L[c] / R.nc[c];
             R.inv_ell[c] = (double)R.nc[c] / R.L[c];
             R.ellf[c] = (float)R.ell[c];
+            R.ell_lo[c] = (float)(R.ell[c] - (double)R.ellf[c]);
         }
         R.cell_off = cell_off;
         R.ncell = R.nc[0] * R.nc[1] * R.nc[2];
@@ -1023,6 +1024,7 @@ md_status md_batch_create(md_box** out, int32_t nrep, const int64_t* n, const do
         if (prec == MD_PREC_FP64) CKS(dev_alloc(b, &d.force64, np3));
         else CKS(dev_alloc(b, &d.force4, b->np));
         CKS(dev_alloc(b, &d.xabsB, np3));
+        CKS(dev_alloc(b, &d.offB, np3));
         CKS(dev_alloc(b, &d.velB, np3));
         CKS(dev_alloc(b, &d.imgB, np3));
         CKS(dev_alloc(b, &d.uidB, b->np));

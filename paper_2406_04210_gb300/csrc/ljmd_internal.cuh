@@ -79,6 +79,7 @@ struct RepDev {
     double ell[3];             // cell edge lengths
     double inv_ell[3];
     float ellf[3];
+    float ell_lo[3];           // ell - ellf: (ellf, ell_lo) is the edge as a double-single pair
     int nc[3];
     int cell_off, ncell;
     int p_off, n;              // first slot, real particles
@@ -152,6 +153,7 @@ struct BoxDev {
     double* force64;           // FP64 forces (FP64 mode), force64[c*np + p]
     // old-order copies during a rebuild
     double* xabsB;
+    double* offB;              // new offsets from the new cell centre (layout of `off`), from k_bin
     double* velB;
     int* imgB;
     int* uidB;
