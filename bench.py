@@ -367,7 +367,8 @@ def bench_temperature_sweep(ljmd, inputs, steps, temps=(0.5, 0.722, 1.0, 1.5, 2.
 
 
 def bench_layouts(ljmd, s, tuning, steps=100,
-                  layouts=((1.0, "zrun"), (1.0, "morton"), (1.15, "zrun"), (1.15, "morton"))):
+                  layouts=((1.0, "zrun"), (1.0, "morton"), (1.08, "zrun"), (1.15, "zrun"), (1.15, "morton"),
+                           (1.22, "zrun"))):
     """A/B of the cell layouts on the same fluid: cell edge over the list
     radius, and the order inside cells (z runs, or a space-filling Morton
     curve over 4 x 4 x 4 sub-cells).  Per layout: in-graph force and list-

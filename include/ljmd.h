@@ -326,7 +326,7 @@ md_status md_get_graph_conditional(md_box* b, int32_t* on);
  * blocks-per-SM candidate, and `reps` forced list builds for each segment
  * length (automatic choice +-2) x list blocks-per-SM candidate, at the
  * current positions; applies the fastest and returns it in t[4] (as
- * md_get_tuning).  It then times the cell layouts (cell_scale 1 and 1.15,
+ * md_get_tuning).  It then times the cell layouts (cell_scale 1, 1.08, 1.15 and 1.22,
  * each in both orders) as a step's cost -- one force evaluation plus a list
  * build spread over the box's observed steps per build (10 before any
  * step) -- and keeps the cheapest (md_get_layout reads it).  The box's state

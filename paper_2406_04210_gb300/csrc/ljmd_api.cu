@@ -1818,7 +1818,7 @@ md_status md_autotune(md_box* b, int32_t reps, int32_t t[4])
         CK(b, cudaStreamSynchronize(b->stream));
         for (auto v : nbv) nb = std::max(nb, v);
         const double spb = (b->steps > 0 && nb > 2) ? std::max(1.0, (double)b->steps / (double)(nb - 2)) : 10.0;
-        const double scales[2] = {1.0, 1.15};
+        const double scales[4] = {1.0, 1.08, 1.15, 1.22};
         double best_cost = 1e300, best_scale = b->cell_scale;
         int best_order = b->order;
         for (double sc : scales)
