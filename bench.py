@@ -620,7 +620,7 @@ def run_gpu(args):
 #: DRAM read + write bytes per particle of one k_force_f32 launch (energy
 #: variant), from an ncu capture of the 256,000-particle fluid (fcc 40^3 x 4,
 #: scaled by the particle count); None when the kernel has changed since.
-DRAM_BYTES_PER_PARTICLE = 417.2
+DRAM_BYTES_PER_PARTICLE = 416.5
 
 
 def main():
