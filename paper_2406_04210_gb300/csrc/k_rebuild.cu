@@ -724,8 +724,9 @@ __global__ void __launch_bounds__(LJ_LIST_THREADS, 3) k_nlist(BoxDev b)
 // of the cell.  The warp streams the candidates of the 27 neighbour cells
 // in chunks of 32: lane t loads candidate t of the chunk (coalesced, the
 // next chunk's load in flight while this one is used), adds the cell's
-// shift and drops it when its distance from the cell's box is beyond the
-// list radius (about a quarter of the 27-cell block lies there); the kept
+// shift and drops it when its distance from the bounding box of the cell's
+// particles is beyond the list radius (at least a quarter of the 27-cell
+// block lies there); the kept
 // candidates (shifted FP32 offset and a 16-bit code: neighbour cell k and
 // index inside it) go to a per-warp ring in shared memory.  Every 32 staged
 // candidates, each lane tests them all against its own particle -- one
@@ -800,12 +801,23 @@ __global__ void __launch_bounds__(LJ_LANE_THREADS, 6) k_nlist_lanes(BoxDev b)
             if (je - js > LJ_TILE_MAX) atomicOr(&b.err[0], LJ_ERRBIT_TILE);   // the 11-bit index: never at LJ densities
         }
         __syncwarp();
-        // the cell's box: offsets from the cell centre within half an edge
-        const float hx = 0.5f * R.ellf[0], hy = 0.5f * R.ellf[1], hz = 0.5f * R.ellf[2];
         for (int ib = 0; ib < n; ib += 32) {
             const bool act = ib + lane < n;
             const int i = cs + (act ? ib + lane : 0);
             float4 pi = posq[i];
+            // the box of this pass's particles (tighter than the cell: the
+            // candidates to test are those within the list radius of it)
+            float lx = act ? pi.x : 1.0e30f, ly = act ? pi.y : 1.0e30f, lz = act ? pi.z : 1.0e30f;
+            float ux = act ? pi.x : -1.0e30f, uy = act ? pi.y : -1.0e30f, uz = act ? pi.z : -1.0e30f;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                lx = fminf(lx, __shfl_xor_sync(0xffffffffu, lx, o));
+                ly = fminf(ly, __shfl_xor_sync(0xffffffffu, ly, o));
+                lz = fminf(lz, __shfl_xor_sync(0xffffffffu, lz, o));
+                ux = fmaxf(ux, __shfl_xor_sync(0xffffffffu, ux, o));
+                uy = fmaxf(uy, __shfl_xor_sync(0xffffffffu, uy, o));
+                uz = fmaxf(uz, __shfl_xor_sync(0xffffffffu, uz, o));
+            }
             if (!act) pi = make_float4(1.0e30f, 1.0e30f, 1.0e30f, 0.f);   // a far point: r^2 is inf
             const float2 nxy = make_float2(-pi.x, -pi.y);
             const float nz = -pi.z;
@@ -896,8 +908,8 @@ __global__ void __launch_bounds__(LJ_LANE_THREADS, 6) k_nlist_lanes(BoxDev b)
                 // stage: shift into the cell's frame, keep what can be within reach of the cell
                 const float4 sh = s_sh[warp][kc];
                 const float qx = cur.x + sh.x, qy = cur.y + sh.y, qz = cur.z + sh.z;
-                const float gx = fmaxf(fabsf(qx) - hx, 0.f), gy = fmaxf(fabsf(qy) - hy, 0.f),
-                            gz = fmaxf(fabsf(qz) - hz, 0.f);
+                const float gx = fmaxf(fmaxf(lx - qx, qx - ux), 0.f), gy = fmaxf(fmaxf(ly - qy, qy - uy), 0.f),
+                            gz = fmaxf(fmaxf(lz - qz, qz - uz), 0.f);
                 const bool keep = lane < len && fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < rcull;
                 const unsigned bal = __ballot_sync(0xffffffffu, keep);
                 if (keep) {
