@@ -290,6 +290,45 @@ __global__ void __launch_bounds__(LJ_CHUNK) k_scatter(BoxDev b)
 }
 
 // ---------------------------------------------------------------------------
+// k_list_work: the cells to rebuild, one block.  The rebuilding replicas in
+// order, with the prefix of their cell counts, so that the per-cell kernels
+// (k_sortgather, k_nlist_lanes) stride over those cells only: a step in which
+// a few replicas of many rebuild does not walk (and test) every cell of the
+// batch.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_list_work(BoxDev b)
+{
+    if (!box_needs_rebuild(b)) return;
+    __shared__ int s_warp[33];
+    int nsel = 0, ncell = 0;
+    for (int base = 0; base < b.nrep; base += blockDim.x) {
+        const int r = base + (int)threadIdx.x;
+        const bool need = r < b.nrep && rep_needs_rebuild(b, r);
+        int tsel, tcell;
+        const int xs = block_excl_scan(need ? 1 : 0, s_warp, tsel);
+        const int xc = block_excl_scan(need ? b.rep[r].ncell : 0, s_warp, tcell);
+        if (need) {
+            b.lw_rep[nsel + xs] = r;
+            b.lw_off[nsel + xs] = ncell + xc;
+        }
+        nsel += tsel;
+        ncell += tcell;
+    }
+    if (threadIdx.x == 0) {
+        b.lw_off[nsel] = ncell;
+        b.lw_hdr[0] = nsel;
+    }
+}
+
+// Cell t of the concatenation of the rebuilding replicas' cells; kr is the
+// replica index of the caller's previous t (t only grows).
+__device__ __forceinline__ int work_cell(const BoxDev& b, int t, int& kr)
+{
+    while (t >= b.lw_off[kr + 1]) ++kr;
+    return b.rep[b.lw_rep[kr]].cell_off + (t - b.lw_off[kr]);
+}
+
+// ---------------------------------------------------------------------------
 // k_sortgather: one warp per cell.  Order the members of the cell by their
 // FP32 z offset from the cell centre (the value posq will hold), ties by
 // user index (count of smaller keys; keys are unique), so the layout is a
@@ -380,10 +419,11 @@ __global__ void __launch_bounds__(256) k_sortgather(BoxDev b)
     }
     const int lane = threadIdx.x & 31;
     const int wpb = blockDim.x >> 5;
-    for (int gc = blockIdx.x * wpb + (threadIdx.x >> 5); gc < b.ncell; gc += gridDim.x * wpb) {
-        int r = b.cell_rep[gc];
-        if (!rep_needs_rebuild(b, r)) continue;   // warp-uniform
-        const RepDev& R = b.rep[r];
+    const int total = b.lw_off[b.lw_hdr[0]];
+    int kr = 0;
+    for (int t = blockIdx.x * wpb + (threadIdx.x >> 5); t < total; t += gridDim.x * wpb) {
+        const int gc = work_cell(b, t, kr);
+        const RepDev& R = b.rep[b.lw_rep[kr]];
         int s0 = b.cell_start[gc];
         int n = b.cell_end[gc] - s0;
         for (int base = 0; base < n; base += 32) {
@@ -781,9 +821,11 @@ __global__ void __launch_bounds__(LJ_LANE_THREADS, 6) k_nlist_lanes(BoxDev b)
     const float4* __restrict__ posq = b.posq;
     int longest = 0;
     const int nwarp = gridDim.x * kLaneWarps;
-    for (int gc = blockIdx.x * kLaneWarps + warp; gc < b.ncell; gc += nwarp) {
-        const int r = b.cell_rep[gc];
-        if (!rep_needs_rebuild(b, r)) continue;   // warp-uniform
+    const int total = b.lw_off[b.lw_hdr[0]];
+    int kr = 0;
+    for (int t = blockIdx.x * kLaneWarps + warp; t < total; t += nwarp) {
+        const int gc = work_cell(b, t, kr);
+        const int r = b.lw_rep[kr];
         const RepDev& R = b.rep[r];
         int cx, cy;
         const int cz = cell_coords(R, gc, cx, cy);
@@ -1023,6 +1065,12 @@ cudaError_t launch_nlist(const BoxDev& b, Launch l)
 // Shared memory of k_nlist_lanes for capacity K: K + 8 16-bit code slots
 // per lane (slot K takes the codes past the capacity).
 size_t nlist_lanes_smem(int K) { return (size_t)LJ_LANE_THREADS * (size_t)(K + 8) * 2u; }
+
+cudaError_t launch_list_work(const BoxDev& b, cudaStream_t s)
+{
+    k_list_work<<<1, 1024, 0, s>>>(b);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_nlist_lanes(const BoxDev& b, Launch l)
 {

@@ -154,6 +154,12 @@ struct BoxDev {
     // old-order copies during a rebuild
     double* xabsB;
     double* offB;              // new offsets from the new cell centre (layout of `off`), from k_bin
+    // cells to rebuild: the rebuilding replicas in order (lw_rep[0 .. lw_hdr[0])) and
+    // the first index of each one's cells in their concatenation (lw_off, one more
+    // entry: the total); written by k_list_work at the head of a rebuild
+    int* lw_hdr;
+    int* lw_rep;
+    int* lw_off;
     double* velB;
     int* imgB;
     int* uidB;
@@ -504,6 +510,7 @@ cudaError_t launch_nlist(const BoxDev& b, Launch l);
 // one warp per cell, one lane per particle (rows staged in shared memory:
 // nlist_lanes_smem(K) bytes per block)
 cudaError_t launch_nlist_lanes(const BoxDev& b, Launch l);
+cudaError_t launch_list_work(const BoxDev& b, cudaStream_t s);   // one block; before the cell kernels
 size_t nlist_lanes_smem(int K);
 // sets a step graph's IF-node condition from the box-wide rebuild word
 cudaError_t launch_set_rebuild_cond(cudaGraphConditionalHandle h, const BoxDev& b, unsigned long long* runs,
