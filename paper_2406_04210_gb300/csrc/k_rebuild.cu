@@ -32,6 +32,20 @@ __device__ __forceinline__ int cell_coords(const RepDev& R, int gc, int& cx, int
     return t / R.nc[1];
 }
 
+// Cell (chunk) t of the concatenation of the rebuilding replicas' cells
+// (particle chunks), from k_list_work's lists; kr is the replica index of the
+// caller's previous t (t only grows).
+__device__ __forceinline__ int work_cell(const BoxDev& b, int t, int& kr)
+{
+    while (t >= b.lw_off[kr + 1]) ++kr;
+    return b.rep[b.lw_rep[kr]].cell_off + (t - b.lw_off[kr]);
+}
+__device__ __forceinline__ int work_chunk(const BoxDev& b, int t, int& kr)
+{
+    while (t >= b.lw_coff[kr + 1]) ++kr;
+    return b.rep[b.lw_rep[kr]].chunk_off + (t - b.lw_coff[kr]);
+}
+
 // 8-byte component c of particle p of an integrator array in the layout of
 // the box precision (FP64: one double; DS: hi/lo floats in two planes).
 __device__ __forceinline__ void copy_acc(const BoxDev& b, double* dst, const double* src, int c,
@@ -107,10 +121,12 @@ __device__ __forceinline__ void store_offB(const BoxDev& b, const RepDev& R, int
 __global__ void __launch_bounds__(LJ_CHUNK) k_bin(BoxDev b, int from_abs)
 {
     if (!box_needs_rebuild(b)) return;
-    for (int w = blockIdx.x; w < b.nchunk; w += gridDim.x) {
+    const int tot = b.lw_coff[b.lw_hdr[0]];
+    int kr = 0;
+    for (int t = blockIdx.x; t < tot; t += gridDim.x) {
+        const int w = work_chunk(b, t, kr);
         int4 ch = b.chunk[w];
         int r = ch.x;
-        if (!rep_needs_rebuild(b, r)) continue;
         int p = ch.y + (int)threadIdx.x;
         const bool act = p < ch.z;   // every lane reaches the warp-wide count below
         if (!act) p = ch.y;
@@ -272,9 +288,10 @@ __global__ void __launch_bounds__(256) k_scan_add(BoxDev b, const int4* tiles, i
 __global__ void __launch_bounds__(LJ_CHUNK) k_scatter(BoxDev b)
 {
     if (!box_needs_rebuild(b)) return;
-    for (int w = blockIdx.x; w < b.nchunk; w += gridDim.x) {
-        int4 ch = b.chunk[w];
-        if (!rep_needs_rebuild(b, ch.x)) continue;
+    const int tot = b.lw_coff[b.lw_hdr[0]];
+    int kr = 0;
+    for (int t = blockIdx.x; t < tot; t += gridDim.x) {
+        int4 ch = b.chunk[work_chunk(b, t, kr)];
         int p = ch.y + (int)threadIdx.x;
         const bool act = p < ch.z;
         // warp-aggregated slot claims: one atomic per distinct cell of the
@@ -290,42 +307,39 @@ __global__ void __launch_bounds__(LJ_CHUNK) k_scatter(BoxDev b)
 }
 
 // ---------------------------------------------------------------------------
-// k_list_work: the cells to rebuild, one block.  The rebuilding replicas in
-// order, with the prefix of their cell counts, so that the per-cell kernels
-// (k_sortgather, k_nlist_lanes) stride over those cells only: a step in which
-// a few replicas of many rebuild does not walk (and test) every cell of the
-// batch.
+// k_list_work: the work of a rebuild, one block.  The rebuilding replicas in
+// order, with the prefixes of their cell and particle-chunk counts, so that
+// the per-cell kernels (k_sortgather, k_nlist_lanes) and the per-chunk ones
+// (k_bin, k_scatter, k_gather) stride over those cells and chunks only: a step
+// in which a few replicas of many rebuild does not walk (and test) every cell
+// and chunk of the batch.  Launched first in every rebuild sequence.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024) k_list_work(BoxDev b)
 {
     if (!box_needs_rebuild(b)) return;
     __shared__ int s_warp[33];
-    int nsel = 0, ncell = 0;
+    int nsel = 0, ncell = 0, nch = 0;
     for (int base = 0; base < b.nrep; base += blockDim.x) {
         const int r = base + (int)threadIdx.x;
         const bool need = r < b.nrep && rep_needs_rebuild(b, r);
-        int tsel, tcell;
+        int tsel, tcell, tch;
         const int xs = block_excl_scan(need ? 1 : 0, s_warp, tsel);
         const int xc = block_excl_scan(need ? b.rep[r].ncell : 0, s_warp, tcell);
+        const int xh = block_excl_scan(need ? b.rep[r].nchunk : 0, s_warp, tch);
         if (need) {
             b.lw_rep[nsel + xs] = r;
             b.lw_off[nsel + xs] = ncell + xc;
+            b.lw_coff[nsel + xs] = nch + xh;
         }
         nsel += tsel;
         ncell += tcell;
+        nch += tch;
     }
     if (threadIdx.x == 0) {
         b.lw_off[nsel] = ncell;
+        b.lw_coff[nsel] = nch;
         b.lw_hdr[0] = nsel;
     }
-}
-
-// Cell t of the concatenation of the rebuilding replicas' cells; kr is the
-// replica index of the caller's previous t (t only grows).
-__device__ __forceinline__ int work_cell(const BoxDev& b, int t, int& kr)
-{
-    while (t >= b.lw_off[kr + 1]) ++kr;
-    return b.rep[b.lw_rep[kr]].cell_off + (t - b.lw_off[kr]);
 }
 
 // ---------------------------------------------------------------------------
@@ -405,9 +419,10 @@ __global__ void __launch_bounds__(256) k_sortgather(BoxDev b)
     if (b.all_pairs) {
         // one cell holds the whole replica and no list needs an order: a
         // particle's slot is its index inside the replica, one thread each
-        for (int w = blockIdx.x; w < b.nchunk; w += gridDim.x) {
-            const int4 ch = b.chunk[w];
-            if (!rep_needs_rebuild(b, ch.x)) continue;   // block-uniform
+        const int tot = b.lw_coff[b.lw_hdr[0]];
+        int kr = 0;
+        for (int t = blockIdx.x; t < tot; t += gridDim.x) {
+            const int4 ch = b.chunk[work_chunk(b, t, kr)];
             const RepDev& R = b.rep[ch.x];
             for (int s = ch.y + (int)threadIdx.x; s < ch.z; s += blockDim.x) {
                 if (s == R.p_off) atomicAdd(&b.nbuild[ch.x], 1ull);   // a re-binning
@@ -449,9 +464,10 @@ __global__ void __launch_bounds__(256) k_sortgather(BoxDev b)
 __global__ void __launch_bounds__(LJ_CHUNK) k_gather(BoxDev b)
 {
     if (b.all_pairs || !box_needs_rebuild(b)) return;
-    for (int w = blockIdx.x; w < b.nchunk; w += gridDim.x) {
-        const int4 ch = b.chunk[w];
-        if (!rep_needs_rebuild(b, ch.x)) continue;   // block-uniform
+    const int tot = b.lw_coff[b.lw_hdr[0]];
+    int kr = 0;
+    for (int t = blockIdx.x; t < tot; t += gridDim.x) {
+        const int4 ch = b.chunk[work_chunk(b, t, kr)];
         const int s = ch.y + (int)threadIdx.x;
         if (s >= ch.z) continue;
         const int p = b.perm[s];

@@ -336,7 +336,7 @@ md_status clear_err(md_box* b)
 // ------------------------------------------------------------------------
 // Kernels of one rebuild sequence (bin, scan x2, scatter, rank, gather,
 // list; all pairs: binning only re-wraps and re-centres).
-int rebuild_kernels(md_box* b) { return b->all_pairs ? 5 : 8; }
+int rebuild_kernels(md_box* b) { return b->all_pairs ? 6 : 8; }
 
 md_status enqueue_rebuild(md_box* b, int from_abs, cudaStream_t s = nullptr)
 {
@@ -346,7 +346,7 @@ md_status enqueue_rebuild(md_box* b, int from_abs, cudaStream_t s = nullptr)
         return l;
     };
     Launch l = on(lch(b));
-    if (!b->all_pairs) CK(b, launch_list_work(b->d, s));   // the cells the per-cell kernels visit
+    CK(b, launch_list_work(b->d, s));   // the cells and chunks the rebuild kernels visit
     CK(b, launch_bin(b->d, from_abs, l));
     Launch lt{std::max(1, std::min((int)b->tiles.size(), b->nsm * 2)), 1024, s};
     CK(b, launch_scan_tiles(b->d, b->d_tiles, (int)b->tiles.size(), b->d_tile_sum, lt));
@@ -1046,10 +1046,11 @@ md_status md_batch_create(md_box** out, int32_t nrep, const int64_t* n, const do
         CKS(dev_alloc(b, &d.nbuild, nrep));
         {
             int* lw;
-            CKS(dev_alloc(b, &lw, 1 + 2 * (size_t)nrep + 1));
+            CKS(dev_alloc(b, &lw, 1 + 3 * (size_t)nrep + 2));
             d.lw_hdr = lw;
             d.lw_rep = lw + 1;
             d.lw_off = lw + 1 + nrep;
+            d.lw_coff = lw + 2 + 2 * nrep;
         }
         CKS(dev_alloc(b, &d.err, 4));
         CKS(dev_alloc(b, &b->d_cond_runs, 1));

@@ -154,12 +154,14 @@ struct BoxDev {
     // old-order copies during a rebuild
     double* xabsB;
     double* offB;              // new offsets from the new cell centre (layout of `off`), from k_bin
-    // cells to rebuild: the rebuilding replicas in order (lw_rep[0 .. lw_hdr[0])) and
-    // the first index of each one's cells in their concatenation (lw_off, one more
-    // entry: the total); written by k_list_work at the head of a rebuild
+    // work of a rebuild: the rebuilding replicas in order (lw_rep[0 .. lw_hdr[0])),
+    // the first index of each one's cells (lw_off) and particle chunks (lw_coff)
+    // in their concatenations (one more entry each: the totals); written by
+    // k_list_work at the head of a rebuild
     int* lw_hdr;
     int* lw_rep;
     int* lw_off;
+    int* lw_coff;
     double* velB;
     int* imgB;
     int* uidB;
