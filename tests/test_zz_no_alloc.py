@@ -57,7 +57,7 @@ def test_force_noalloc_allocates_nothing_on_a_fresh_box(ljmd):
     # device's free memory; then the same results as md_force
     import torch
     s = inputs.lj4000()
-    # the once-per-device set-up (the scratch array's address; the driver may
+    # the once-per-device set-up (the scratch array's address; the CUDA driver may
     # load the library's module then) is done first, on another box
     a = ljmd.from_system(inputs.fcc_system(6, seed=7), "mixed_ds")
     assert a._lib.md_force_noalloc(a._h, None, None, None) == 0
