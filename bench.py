@@ -119,17 +119,17 @@ def _gpu_smi_id(dev):
 # ----------------------------------------------------------------------------
 def host_cpu():
     """(nproc, CPU model) of this host, for the CPU-baseline lines."""
-    model = None
+    fields = {}
     try:
         with open("/proc/cpuinfo") as f:
             for ln in f:
                 k, _, v = ln.partition(":")
                 k = k.strip().lower()
-                if k in ("model name", "model", "cpu model", "hardware") and v.strip():
-                    model = v.strip()
-                    break
+                if v.strip() and k not in fields:
+                    fields[k] = v.strip()
     except OSError:
         pass
+    model = fields.get("model name") or fields.get("cpu model") or fields.get("hardware")
     if not model:
         try:
             out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
@@ -139,6 +139,7 @@ def host_cpu():
                     break
         except Exception:
             pass
+    model = model or fields.get("model")
     import platform
     return os.cpu_count(), model or platform.machine()
 
