@@ -491,8 +491,7 @@ def run_gpu(args):
     box.list_kernel = args.list_kernel
     if args.cond_graph:
         box.graph_conditional = True
-    tuning = box.autotune(reps=3, cache=False)        # launch/layout autotuner
-    tuning["list_kernel"] = box.list_kernel
+    tuning = box.autotune(reps=3, cache=False)        # launch/layout/list-kernel autotuner
     thermo = torch.zeros((max(args.steps, args.warmup, 1), 1, 4), dtype=torch.float64,
                          device="cuda")
     if args.warmup:

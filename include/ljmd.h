@@ -329,8 +329,11 @@ md_status md_get_graph_conditional(md_box* b, int32_t* on);
  * md_get_tuning).  It then times the cell layouts (cell_scale 1, 1.08, 1.15 and 1.22,
  * each in both orders) as a step's cost -- one force evaluation plus a list
  * build spread over the box's observed steps per build (10 before any
- * step) -- and keeps the cheapest (md_get_layout reads it).  The box's state
- * is unchanged apart from a list rebuild. */
+ * step) -- and keeps the cheapest (md_get_layout reads it).  With the list
+ * kernel on MD_LIST_AUTO it times both list kernels over the layouts and
+ * sets the cheaper one (md_get_list_kernel reads it); a kernel set by
+ * md_set_list_kernel is kept.  The box's state is unchanged apart from a list
+ * rebuild. */
 md_status md_autotune(md_box* b, int32_t reps, int32_t t[4]);
 
 /* Phase timing of md_integrate.  md_set_profiling(b, 1) resets the counters

@@ -1831,8 +1831,18 @@ md_status md_autotune(md_box* b, int32_t reps, int32_t t[4])
         const double scales[4] = {1.0, 1.08, 1.15, 1.22};
         double best_cost = 1e300, best_scale = b->cell_scale;
         int best_order = b->order;
+        // the list-build kernel too, unless the caller fixed it
+        const int fixed_kind = b->list_kernel;
+        const int kinds[2] = {MD_LIST_LANES, MD_LIST_QUADS};
+        const int nkind = fixed_kind == MD_LIST_AUTO ? 2 : 1;
+        int best_kind = fixed_kind;
+        for (int ki = 0; ki < nkind; ++ki)
         for (double sc : scales)
             for (int od = 0; od < 2; ++od) {
+                if (fixed_kind == MD_LIST_AUTO && b->list_kernel != kinds[ki]) {
+                    b->list_kernel = kinds[ki];
+                    invalidate_graphs(b);
+                }
                 const md_status st = set_layout(b, sc, od);
                 if (st == MD_ERR_CAPACITY) continue;   // its tiles overflow: not a candidate
                 if (st != MD_OK) return st;
@@ -1857,8 +1867,15 @@ md_status md_autotune(md_box* b, int32_t reps, int32_t t[4])
                     best_cost = cost;
                     best_scale = sc;
                     best_order = od;
+                    best_kind = b->list_kernel;
                 }
             }
+        if (b->list_kernel != best_kind) {
+            b->list_kernel = best_kind;
+            invalidate_graphs(b);
+            // a layout the other kernel refuses is re-gridded by set_layout below
+            if (b->cell_scale == best_scale && b->order == best_order) CKS(full_rebuild(b));
+        }
         CKS(set_layout(b, best_scale, best_order));
     }
     CKS(leave(b));

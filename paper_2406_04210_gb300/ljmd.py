@@ -406,6 +406,9 @@ class Box:
             if key in table:
                 ent = dict(table[key])
                 lay = {k: ent.pop(k) for k in ("cell_scale", "order") if k in ent}
+                kind = ent.pop("list_kernel", None)
+                if kind is not None:
+                    self.list_kernel = kind
                 self.set_tuning(**ent)
                 if lay:
                     self.set_layout(**lay)
@@ -414,6 +417,7 @@ class Box:
         self._check(self._lib.md_autotune(self._h, int(reps), t.ctypes.data), "md_autotune")
         res = dict(zip(self.TUNING, (int(x) for x in t)))
         res.update(self.layout())
+        res["list_kernel"] = self.list_kernel
         if cache and path:
             try:
                 os.makedirs(os.path.dirname(path), exist_ok=True)

@@ -293,6 +293,7 @@ def test_autotune_keeps_results(ljmd):
     t = b.autotune(reps=2, cache=False)
     assert 1 <= t["force_blocks_per_sm"] <= 32 and 1 <= t["list_blocks_per_sm"] <= 32
     assert 1 <= t["segment_cells"] <= 16
+    assert t["list_kernel"] in ("lanes", "quads") and b.list_kernel == t["list_kernel"]
     f1, e1, _ = b.force()
     S = pair_scale(s.box, s.pos, _lj(s))
     assert (np.linalg.norm(f1 - f0, axis=1) / S).max() <= 1e-5
@@ -303,6 +304,15 @@ def test_autotune_keeps_results(ljmd):
     d = b.get_state()[0] - r["pos"]
     d -= s.box * np.rint(d / s.box)
     assert np.abs(d).max() <= 1e-4
+
+
+def test_autotune_keeps_a_chosen_list_kernel(ljmd):
+    s = inputs.lj4000()
+    b = ljmd.from_system(s, "mixed_ds")
+    b.list_kernel = "quads"
+    t = b.autotune(reps=1, cache=False)
+    assert t["list_kernel"] == "quads" and b.list_kernel == "quads"
+    check_lists(b, s, 2.8)
 
 
 @pytest.mark.parametrize("scale,order", [(1.0, "morton"), (1.3, "zrun"), (1.3, "morton")])
