@@ -332,8 +332,9 @@ md_status md_get_graph_conditional(md_box* b, int32_t* on);
  * step) -- and keeps the cheapest (md_get_layout reads it).  With the list
  * kernel on MD_LIST_AUTO it times both list kernels over the layouts and
  * sets the cheaper one (md_get_list_kernel reads it); a kernel set by
- * md_set_list_kernel is kept.  The box's state is unchanged apart from a list
- * rebuild. */
+ * md_set_list_kernel is kept.  Last it times the list build's blocks per SM
+ * again at the chosen layout and kernel.  The box's state is unchanged apart
+ * from a list rebuild. */
 md_status md_autotune(md_box* b, int32_t reps, int32_t t[4]);
 
 /* Phase timing of md_integrate.  md_set_profiling(b, 1) resets the counters

@@ -1877,6 +1877,30 @@ md_status md_autotune(md_box* b, int32_t reps, int32_t t[4])
             if (b->cell_scale == best_scale && b->order == best_order) CKS(full_rebuild(b));
         }
         CKS(set_layout(b, best_scale, best_order));
+        // the list build's grid again, at the chosen layout and kernel
+        float best_g = 1e30f;
+        int best_gl = b->list_per_sm;
+        for (int lc : {3, 4, 6, 8, 12, 16, 24}) {
+            b->list_per_sm = lc;
+            float ms;
+            CKS(time_launches(b, reps, [&]() -> md_status {
+                CKS(set_all_rebuild(b));
+                return enqueue_rebuild(b, b->fresh_abs ? 1 : 0);
+            }, &ms));
+            int e2[3];
+            CKS(read_err(b, e2));
+            if (e2[0] & (LJ_ERRBIT_TILE | LJ_ERRBIT_CAPACITY)) {
+                CKS(clear_err(b));
+                continue;
+            }
+            if (ms < best_g) {
+                best_g = ms;
+                best_gl = lc;
+            }
+        }
+        b->list_per_sm = best_gl;
+        invalidate_graphs(b);
+        CKS(full_rebuild(b));
     }
     CKS(leave(b));
     return md_get_tuning(b, t);
