@@ -191,6 +191,31 @@ def test_batched_replicas_match_single_boxes(ljmd):
         o += x.n
 
 
+def test_replicas_rebuilding_at_different_steps_keep_exact_lists(ljmd):
+    # replicas at different temperatures rebuild at different steps: each
+    # rebuild visits only the rebuilding replicas' cells and chunks; every
+    # replica's lists still equal the FP64 definition at the positions they
+    # were built from
+    systems = inputs.replica_systems(nrep=6, nmin=500, nmax=3000, seed=11, T_range=(0.5, 2.5))
+    n = [x.n for x in systems]
+    pos = np.concatenate([x.pos for x in systems])
+    vel = np.concatenate([x.vel for x in systems])
+    box = np.stack([x.box for x in systems])
+    b = ljmd.Box(pos, box, vel, n=n, precision="mixed_ds")
+    b.set_lj(1.0, 1.0, 2.5, 0.3)
+    b.integrate(0.005, 60, thermo=False)
+    assert b.info().rebuilds >= 3
+    count, nbr, pos_used = b.nlist()
+    o = 0
+    for x in systems:
+        ref = oracle.nlist(x.box, pos_used[o:o + x.n], 2.8)
+        assert np.array_equal(count[o:o + x.n], ref.count)
+        for i in range(x.n):
+            got = np.sort(nbr[o + i, : count[o + i]]) - o
+            assert np.array_equal(got, ref.list[i, : ref.count[i]]), i
+        o += x.n
+
+
 def test_capacity_overflow_recovers(ljmd):
     s = inputs.lj4000()
     ref = ljmd.from_system(s, "mixed_ds")
@@ -271,6 +296,22 @@ def test_box_too_small_rejected(ljmd):
     with pytest.raises(ljmd.MDError) as ei:
         b.set_lj(1.0, 1.0, 2.5, 0.3)
     assert ei.value.status == 5
+
+
+def test_layout_kernel_and_graph_options_are_checked(ljmd):
+    # out-of-range options are refused with MD_ERR_ARG and change nothing
+    s = inputs.lj4000()
+    b = ljmd.from_system(s, "mixed_ds")
+    lib, h = b._lib, b._h
+    assert lib.md_set_layout(h, 0.9, 0) == 1          # cell edge below the list radius
+    assert lib.md_set_layout(h, float("nan"), 0) == 1
+    assert lib.md_set_layout(h, 1.0, 2) == 1          # no such order
+    assert lib.md_set_list_kernel(h, 3) == 1
+    assert lib.md_set_list_kernel(h, -1) == 1
+    assert lib.md_set_graph_conditional(h, 2) == 1
+    assert b.layout() == {"cell_scale": 1.0, "order": "zrun"}
+    assert b.list_kernel == "auto" and not b.graph_conditional
+    check_lists(b, s, 2.8)
 
 
 def test_torch_device_arrays(ljmd):
