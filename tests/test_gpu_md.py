@@ -149,6 +149,27 @@ def test_small_and_degenerate_boxes(ljmd, n, L):
     np.testing.assert_allclose(f, fo, rtol=0, atol=1e-11 * max(1.0, np.abs(fo).max()))
 
 
+@pytest.mark.parametrize("scale", [1.5, 2.0])
+def test_one_and_two_cells_per_edge(ljmd, scale):
+    # cells larger than a third of the box: 2 (scale 1.5) or 1 (scale 2.0)
+    # cell per edge, so neighbour cells repeat with different image shifts
+    n, L = 700, 8.41
+    rng = np.random.default_rng(n)
+    box = np.array([L, L, L])
+    pos = rng.uniform(0, L, size=(n, 3))
+    pos, _, _ = oracle.fire(box, pos, oracle.LJ.single(), maxit=200, ftol=1.0)
+    b = ljmd.Box(pos, box, None, precision="mixed_ds")
+    b.set_lj(1.0, 1.0, 2.5, 0.3)
+    b.set_layout(cell_scale=scale)
+    s = inputs.System(box, pos, np.zeros((n, 3)), np.zeros(n, np.int32), np.ones((1, 1)), np.ones((1, 1)),
+                      np.full((1, 1), 2.5))
+    check_lists(b, s, 2.8)
+    f, e, w = b.force()
+    fo, eo, wo = oracle.forces_brute(box, pos, oracle.LJ.single())
+    S = pair_scale(box, pos, oracle.LJ.single())
+    assert (np.linalg.norm(f - fo, axis=1) / S).max() <= 1e-5
+
+
 def test_cell_faces_and_boundaries(ljmd):
     # particles exactly on cell faces, at x = 0 and just below L
     rl = 2.8
