@@ -48,6 +48,31 @@ __device__ __forceinline__ bool tstat_collide(const BoxDev& b, const RepDev& R, 
     return true;
 }
 
+// The all-pairs form (one cell per replica, offsets from the box centre):
+// the drift keeps each offset in [-L/2, L/2) itself, counting the image, so
+// the form needs no re-binning between steps (there are no lists).
+__device__ __forceinline__ void wrap_ds(const BoxDev& b, const RepDev& R, int c, int p, float& oh, float& ol)
+{
+    const float lh = (float)R.L[c], ll = (float)(R.L[c] - (double)lh);
+    if (oh >= 0.5f * lh) {
+        ds_add_ds(oh, ol, -lh, -ll);
+        b.img[c * b.np + p] += 1;
+    } else if (oh < -0.5f * lh) {
+        ds_add_ds(oh, ol, lh, ll);
+        b.img[c * b.np + p] -= 1;
+    }
+}
+__device__ __forceinline__ void wrap_d(const BoxDev& b, const RepDev& R, int c, int p, double& x)
+{
+    if (x >= 0.5 * R.L[c]) {
+        x -= R.L[c];
+        b.img[c * b.np + p] += 1;
+    } else if (x < -0.5 * R.L[c]) {
+        x += R.L[c];
+        b.img[c * b.np + p] -= 1;
+    }
+}
+
 // sidx: this launch finalizes step (*b.step_ctr + sidx) (MID and LAST modes).
 template <int ACC, bool FORCE64, int MODE, bool ENERGY, bool TSTAT>
 __global__ void __launch_bounds__(LJ_CHUNK) k_integrate(BoxDev b, double dt, int sidx)
@@ -100,6 +125,7 @@ __global__ void __launch_bounds__(LJ_CHUNK) k_integrate(BoxDev b, double dt, int
                         float ph, pl;
                         ds_mul_ds(dt_h, dt_l, vh, vl, ph, pl);
                         ds_add_ds(oh, ol, ph, pl);
+                        if (b.all_pairs) wrap_ds(b, b.rep[r], c, p, oh, ol);
                         offf[c * np + p] = oh;
                         offf[3 * np + c * np + p] = ol;
                         o[c] = oh;
@@ -119,13 +145,16 @@ __global__ void __launch_bounds__(LJ_CHUNK) k_integrate(BoxDev b, double dt, int
                     if (MODE != LJ_STEP_LAST) {
                         v = v + hdt * F[c];
                         double x = b.off[c * np + p] + dt * v;
+                        if (b.all_pairs) wrap_d(b, b.rep[r], c, p, x);
                         b.off[c * np + p] = x;
                         o[c] = __double2float_rn(x);
                     }
                     b.vel[c * np + p] = v;
                 }
             }
-            if (MODE != LJ_STEP_LAST) {
+            if (MODE != LJ_STEP_LAST && b.all_pairs) {
+                b.posq[p] = make_float4(o[0], o[1], o[2], __int_as_float(b.type[p]));
+            } else if (MODE != LJ_STEP_LAST) {
                 float4 rf = b.ref[p];
                 b.posq[p] = make_float4(o[0], o[1], o[2], __int_as_float(b.type[p]));
                 float ddx = o[0] - rf.x, ddy = o[1] - rf.y, ddz = o[2] - rf.z;

@@ -735,7 +735,7 @@ md_status enqueue_steps(md_box* b, int64_t n, double dt, int energy, double* rin
         }
         if (s == n) break;
         CK(b, mark(s, 1, 0, b->stream));
-        CKS(enqueue_rebuild_step(b));
+        if (!b->all_pairs) CKS(enqueue_rebuild_step(b));   // all pairs: the drift keeps offsets wrapped
         CK(b, mark(s, 1, 1, b->stream));
         CK(b, join());
         CK(b, mark(s, 2, 0, b->stream));
