@@ -489,6 +489,7 @@ def run_gpu(args):
     n = s.n
     box = ljmd.from_system(s, "mixed_ds")
     box.list_kernel = args.list_kernel
+    box.force_kernel = args.force_kernel
     if args.cond_graph:
         box.graph_conditional = True
     tuning = box.autotune(reps=3, cache=False)        # launch/layout/list-kernel autotuner
@@ -520,6 +521,7 @@ def run_gpu(args):
     prof = box.profile()
 
     # roofline of the dominant kernel (pair force), timed in the graph
+    fk = "tiles" if box.force_kernel == "tiles" else "chunks"   # "auto" runs the chunk kernel
     f_ms, f_n = prof["force"]
     f_avg = f_ms / max(f_n, 1)
     list_entries = info1.list_entries
@@ -596,8 +598,8 @@ def run_gpu(args):
         "data": "synthetic", "config": dict(WORKLOAD, parallelism=f"replicas{world}"),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
-                     "traffic": (DRAM_BYTES_PER_PARTICLE * n) if DRAM_BYTES_PER_PARTICLE else None,
-                     "kernel": "k_force_f32 (pair force, energy+virial)",
+                     "traffic": (DRAM_BYTES_PER_PARTICLE[fk] * n) if DRAM_BYTES_PER_PARTICLE.get(fk) else None,
+                     "kernel": FORCE_KERNEL_NAMES[fk] + " (pair force, energy+virial)",
                      "bytes_per_launch": force_bytes, "avg_launch_ms": f_avg,
                      "peak_kind": f"hbm_gbs of {peak_kind} peaks (copy, burst)"},
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
@@ -618,10 +620,12 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-#: DRAM read + write bytes per particle of one k_force_f32 launch (energy
-#: variant), from an ncu capture of the 256,000-particle fluid (fcc 40^3 x 4,
-#: scaled by the particle count); None when the kernel has changed since.
-DRAM_BYTES_PER_PARTICLE = 416.5
+#: DRAM read + write bytes per particle of one force launch (energy variant)
+#: per force kernel, from an ncu capture of the 256,000-particle fluid (fcc
+#: 40^3 x 4, scaled by the particle count); None when the kernel has changed
+#: since.
+DRAM_BYTES_PER_PARTICLE = {"chunks": 416.5, "tiles": None}
+FORCE_KERNEL_NAMES = {"chunks": "k_force_f32", "tiles": "k_force_tile_f32"}
 
 
 def main():
@@ -638,6 +642,8 @@ def main():
                     help="with --quick: still run the cell-layout A/B")
     ap.add_argument("--list-kernel", default="auto", choices=["auto", "quads", "lanes"],
                     help="list-build kernel (md_set_list_kernel)")
+    ap.add_argument("--force-kernel", default="auto", choices=["auto", "chunks", "tiles"],
+                    help="FP32 list-form force kernel (md_set_force_kernel)")
     ap.add_argument("--cond-graph", action="store_true",
                     help="list update of each step as a conditional graph node (md_set_graph_conditional; "
                          "fewer launches, ~4.5 us slower per step on GB300)")

@@ -310,6 +310,29 @@ enum { MD_LIST_AUTO = 0, MD_LIST_QUADS = 1, MD_LIST_LANES = 2 };
 md_status md_set_list_kernel(md_box* b, int32_t kind);
 md_status md_get_list_kernel(md_box* b, int32_t* kind);
 
+/* FP32 pair-force kernel of the list form (Sec. 4/5: LJ pair forces over the
+ * Verlet lists; Sec. 5 finds that kernel bound by fetching neighbour data).
+ * Both give the forces, energy and virial of the same lists, equal up to
+ * FP32 rounding:
+ *   MD_FORCE_CHUNKS  work items of 128 consecutive particles, 4 threads per
+ *                    particle, neighbour offsets gathered from global memory
+ *                    through L1, the image shift decoded from each entry
+ *   MD_FORCE_TILES   work items of up to 2 x 2 x 2 cells ("bricks"): the
+ *                    brick's neighbourhood (up to 4 x 4 x 4 cells, at most
+ *                    2048 particles) staged in shared memory in the frame of
+ *                    the brick's centre, 4 threads per particle, two pairs at
+ *                    a time in FP32-pair arithmetic; a brick with a larger
+ *                    neighbourhood is evaluated from global memory
+ *   MD_FORCE_AUTO    (default) MD_FORCE_CHUNKS until md_autotune times both
+ *                    and sets the faster one
+ * On the 4M-particle fluid the chunk kernel is the faster (0.54 against
+ * 0.66 ms per launch on GB300).  The FP64 precision and the all-pairs form
+ * have kernels of their own and ignore the setting.  md_force_noalloc always uses MD_FORCE_CHUNKS.  Takes
+ * effect at the next force evaluation; MD_ERR_ARG for another kind. */
+enum { MD_FORCE_AUTO = 0, MD_FORCE_CHUNKS = 1, MD_FORCE_TILES = 2 };
+md_status md_set_force_kernel(md_box* b, int32_t kind);
+md_status md_get_force_kernel(md_box* b, int32_t* kind);
+
 /* Step graphs: with on = 1 the list update of each captured step is a
  * conditional (IF) node, so steps without a list build launch one tiny kernel
  * instead of the rebuild sequence; with on = 0 (default) the rebuild kernels
@@ -332,8 +355,10 @@ md_status md_get_graph_conditional(md_box* b, int32_t* on);
  * step) -- and keeps the cheapest (md_get_layout reads it).  With the list
  * kernel on MD_LIST_AUTO it times both list kernels over the layouts and
  * sets the cheaper one (md_get_list_kernel reads it); a kernel set by
- * md_set_list_kernel is kept.  Last it times the list build's blocks per SM
- * again at the chosen layout and kernel.  The box's state is unchanged apart
+ * md_set_list_kernel is kept.  Then it times the list build's blocks per SM
+ * again at the chosen layout and kernel.  Last, with the force kernel on
+ * MD_FORCE_AUTO, it times both FP32 force kernels and sets the faster one
+ * (md_get_force_kernel reads it).  The box's state is unchanged apart
  * from a list rebuild. */
 md_status md_autotune(md_box* b, int32_t reps, int32_t t[4]);
 

@@ -227,6 +227,360 @@ __global__ void __launch_bounds__(LJ_FORCE_THREADS, SINGLE ? 8 : 6) k_force_f32(
     }
 }
 
+// ---------------------------------------------------------------------------
+// Tiled FP32 pair force (Sec. 4/5: the same forces, energy and virial as
+// k_force_f32; Sec. 5 finds the force kernel bound by fetching neighbour
+// data, which here comes from shared memory).  A block takes one brick of up
+// to 2 x 2 x 2 cells at a time.  It stages the FP32 offsets of the brick's
+// neighbourhood (its cells and the layer of cells around them, up to 64
+// cells) as x, y and z planes of a shared-memory tile, each moved into the
+// frame of the brick's centre by one FMA (q_j = o_j + a ell, a a multiple
+// of 1/2, one rounding), then the brick's particles walk their list rows,
+// LJ_TPP threads per particle, four entries per thread and 16-entry row
+// block.  An entry (stencil digits of neighbour cell k, slot j) names the
+// tile element j - start + base of the tile cell at the particle's cell plus
+// k: its byte address is (entry << 2) plus a table word of the particle's
+// cell indexed by the digits, which also cancels what the shift leaves of
+// the digits -- one shift-add per entry, no decode and no image shift per
+// pair.  Pairs are evaluated two at a time with FP32-pair arithmetic on
+// d' = q_j - p_i = -d_ij (p_i = o_i + a_i ell, the sums negated at the
+// end).  Brick edges are 2 cells only where a tile coordinate stays below 8
+// (one rounding of 2^-22 at most); a brick whose neighbourhood holds more
+// than LJ_BRICK_TILE particles is evaluated from global memory as in
+// k_force_f32.  Energy and virial: one double-single (E_pot, W) share per
+// warp and brick, summed in FP64 by k_thermo in a fixed order.
+// ---------------------------------------------------------------------------
+
+// x, y, z of the tile element at byte address a (planes PL bytes apart)
+template <int PL>
+__device__ __forceinline__ void tile_xyz(uint32_t a, float& x, float& y, float& z)
+{
+    asm("ld.shared.f32 %0, [%3];\n\t"
+        "ld.shared.f32 %1, [%3+%4];\n\t"
+        "ld.shared.f32 %2, [%3+%5];"
+        : "=f"(x), "=f"(y), "=f"(z)
+        : "r"(a), "n"(PL), "n"(2 * PL));
+}
+template <int PL>
+__device__ __forceinline__ int tile_type(uint32_t a)
+{
+    int t;
+    asm("ld.shared.b32 %0, [%1+%2];" : "=r"(t) : "r"(a), "n"(3 * PL));
+    return t;
+}
+
+struct PairAcc2 {
+    float2 fx, fy, fz, e, w;
+};
+
+// Two pair terms (tile elements at a0, a1) against particle i (n = -p_i),
+// accumulated as FP32 pairs; masked, not branched, by the cutoff test.
+template <bool MONO, bool ENERGY, int PL>
+__device__ __forceinline__ void tile_pair2(uint32_t a0, uint32_t a1, const float2& nx, const float2& ny,
+                                           const float2& nz, int ti, int nt, const float4* s_lj,
+                                           const float* s_rc2, const float* s_esh, const float4& mlj,
+                                           float mrc2, float mesh, PairAcc2& A)
+{
+    float x0, y0, z0, x1, y1, z1;
+    tile_xyz<PL>(a0, x0, y0, z0);
+    tile_xyz<PL>(a1, x1, y1, z1);
+    const float2 dx = __fadd2_rn(make_float2(x0, x1), nx);
+    const float2 dy = __fadd2_rn(make_float2(y0, y1), ny);
+    const float2 dz = __fadd2_rn(make_float2(z0, z1), nz);
+    const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+    float2 c12, nc6, e12, ne6, rc2, nesh;
+    if (MONO) {
+        c12 = make_float2(mlj.x, mlj.x);
+        nc6 = make_float2(-mlj.y, -mlj.y);
+        e12 = make_float2(mlj.z, mlj.z);
+        ne6 = make_float2(-mlj.w, -mlj.w);
+        rc2 = make_float2(mrc2, mrc2);
+        nesh = make_float2(-mesh, -mesh);
+    } else {
+        const int p0 = ti * nt + tile_type<PL>(a0), p1 = ti * nt + tile_type<PL>(a1);
+        const float4 q0 = s_lj[p0], q1 = s_lj[p1];
+        c12 = make_float2(q0.x, q1.x);
+        nc6 = make_float2(-q0.y, -q1.y);
+        e12 = make_float2(q0.z, q1.z);
+        ne6 = make_float2(-q0.w, -q1.w);
+        rc2 = make_float2(s_rc2[p0], s_rc2[p1]);
+        nesh = ENERGY ? make_float2(-s_esh[p0], -s_esh[p1]) : make_float2(0.f, 0.f);
+    }
+    const float2 ri = make_float2(rcp_approx(r2.x), rcp_approx(r2.y));
+    const float2 r6 = __fmul2_rn(__fmul2_rn(ri, ri), ri);
+    float2 f = __fmul2_rn(__fmul2_rn(ri, r6), __ffma2_rn(c12, r6, nc6));
+    const bool in0 = r2.x < rc2.x, in1 = r2.y < rc2.y;
+    f.x = in0 ? f.x : 0.f;
+    f.y = in1 ? f.y : 0.f;
+    A.fx = __ffma2_rn(f, dx, A.fx);
+    A.fy = __ffma2_rn(f, dy, A.fy);
+    A.fz = __ffma2_rn(f, dz, A.fz);
+    if (ENERGY) {
+        float2 u = __ffma2_rn(r6, __ffma2_rn(e12, r6, ne6), nesh);
+        u.x = in0 ? u.x : 0.f;
+        u.y = in1 ? u.y : 0.f;
+        A.e = __fadd2_rn(A.e, u);
+        A.w = __ffma2_rn(f, r2, A.w);
+    }
+}
+
+// tile address of entry e for the particle's address table D
+__device__ __forceinline__ uint32_t tile_addr(uint32_t e, const uint32_t* D) { return (e << 2) + D[e >> 26]; }
+
+static_assert(LJ_BRICK_WARPS == LJ_FORCE_WARPS, "per-brick shares in the chunk kernel's share stride");
+constexpr int kBrickThreads = LJ_BRICK_THREADS;
+constexpr int kBrickWarps = kBrickThreads / 32;
+constexpr int kBrickPass = kBrickThreads / LJ_TPP;   // particles per block pass
+template <bool MONO, bool ENERGY>
+__global__ void __launch_bounds__(LJ_BRICK_THREADS, 5) k_force_tile_f32(BoxDev b)
+{
+    constexpr int T = LJ_BRICK_TILE;
+    constexpr int NPL = MONO ? 3 : 4;   // x, y, z (and type) planes
+    constexpr int PL = (T + 1) * 4;     // bytes per plane; element T of each is the sentinel
+    constexpr unsigned FULL = 0xffffffffu;
+    __shared__ __align__(16) float s_t[NPL][T + 1];
+    __shared__ uint32_t s_D[8][64];     // per brick cell and stencil-digit code: tile address term
+    __shared__ int s_tb[64], s_ts[64], s_tn[64];   // tile cells: base in the tile, first slot, particles
+    __shared__ int s_pc[9], s_cs[8];    // brick cells: particle prefix, first slot
+    __shared__ int s_tot;
+    __shared__ float4 s_lj[MONO ? 1 : LJ_MAXT * LJ_MAXT];
+    __shared__ float s_rc2[MONO ? 1 : LJ_MAXT * LJ_MAXT];
+    __shared__ float s_esh[MONO ? 1 : LJ_MAXT * LJ_MAXT];
+    const int nt = b.nt;
+    if (!MONO) {
+        const LJDev* lj = b.lj;
+        for (int k = threadIdx.x; k < nt * nt; k += blockDim.x) {
+            s_lj[k] = make_float4(lj->c12[k], lj->c6[k], lj->e12[k], lj->e6[k]);
+            s_rc2[k] = lj->rc2[k];
+            s_esh[k] = lj->shift[k];
+        }
+    }
+    if (threadIdx.x < NPL) s_t[threadIdx.x][T] = threadIdx.x < 3 ? LJ_SENTINEL_OFF : 0.f;   // type 0
+    const uint32_t X0 = (uint32_t)__cvta_generic_to_shared(&s_t[0][0]);
+    const uint32_t SENT = X0 + 4u * (uint32_t)T;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int grp = threadIdx.x / LJ_TPP, l4 = threadIdx.x % LJ_TPP;
+    const int K = b.K;
+    const float4* __restrict__ posq = b.posq;
+    const float4 mlj = b.c1;
+    const float mrc2 = b.rc2_1, mesh = b.esh_1;
+    const unsigned sent_ent = entry_make(13, b.np);
+    for (int bi = blockIdx.x; bi < b.nbrick; bi += gridDim.x) {
+        const int4 B = b.brick[bi];
+        const int r = B.x;
+        const RepDev& R = b.rep[r];
+        const int ex = min(R.br[0], R.nc[0] - B.y), ey = min(R.br[1], R.nc[1] - B.z),
+                  ez = min(R.br[2], R.nc[2] - B.w);
+        const int tx = ex + 2, txy = tx * (ey + 2), ntc = txy * (ez + 2), nbc = ex * ey * ez;
+        // brick cell cl = u + ex (v + ey w), extents 1 or 2: u = cl & sx,
+        // v = (cl >> sx) & sy, w = cl >> (sx + sy)
+        const int sx = ex - 1, sy = ey - 1;
+        const float3 ell = make_float3(R.ellf[0], R.ellf[1], R.ellf[2]);
+        // tile coordinate t along an axis (brick cell u is t = u + 1): its
+        // offset in cells from the brick centre, t - (extent + 1) / 2
+        const float hx = 0.5f * (float)(ex + 1), hy = 0.5f * (float)(ey + 1), hz = 0.5f * (float)(ez + 1);
+        if (threadIdx.x == 0) {
+            if (bi == 0) *b.any_req = 0;   // the list update of this step has run
+            if (B.y == 0 && B.z == 0 && B.w == 0) {   // the replica's first brick: clear its rebuild triggers
+                b.disp_max[r] = 0u;
+                b.rebuild_req[r] = 0;
+            }
+        }
+        if (warp == 0) {
+            // tile cells 2 lane and 2 lane + 1: first slot and particles, then
+            // their bases (exclusive prefix over the tile)
+            int js[2] = {0, 0}, nk[2] = {0, 0};
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int t = 2 * lane + u;
+                if (t < ntc) {
+                    const int a = t % tx, c = t / txy, bb = (t / tx) - c * (ey + 2);
+                    const int cn = R.cell_off + wrapi(B.y - 1 + a, R.nc[0]) +
+                                   R.nc[0] * (wrapi(B.z - 1 + bb, R.nc[1]) + R.nc[1] * wrapi(B.w - 1 + c, R.nc[2]));
+                    js[u] = b.cell_start[cn];
+                    nk[u] = b.cell_end[cn] - js[u];
+                }
+            }
+            int incl = nk[0] + nk[1];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(FULL, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const int e0 = incl - nk[0] - nk[1];
+            s_tb[2 * lane] = e0;
+            s_tb[2 * lane + 1] = e0 + nk[0];
+            s_ts[2 * lane] = js[0];
+            s_ts[2 * lane + 1] = js[1];
+            s_tn[2 * lane] = nk[0];
+            s_tn[2 * lane + 1] = nk[1];
+            if (lane == 31) s_tot = incl;
+            __syncwarp();
+            // brick cells (lane < 8): first slot and particle prefix
+            int n8 = 0;
+            if (lane < nbc) {
+                const int u = lane & sx, v = (lane >> sx) & sy, w = lane >> (sx + sy);
+                const int t = (u + 1) + tx * (v + 1) + txy * (w + 1);
+                s_cs[lane] = s_ts[t];
+                n8 = s_tn[t];
+            }
+            int inc8 = n8;
+#pragma unroll
+            for (int o = 1; o < 8; o <<= 1) {
+                const int t = __shfl_up_sync(FULL, inc8, o);
+                if (lane >= o) inc8 += t;
+            }
+            if (lane < 8) s_pc[lane + 1] = inc8;   // lanes past the brick's cells add nothing
+            if (lane == 0) s_pc[0] = 0;
+        }
+        __syncthreads();   // tile cell table complete
+        const bool tiled = s_tot <= T;   // block-uniform
+        const int npb = s_pc[8];
+        if (tiled) {
+            // a row of the tile (tile cells along x at one y, z) is one run of
+            // tile elements; a warp stages whole rows, up to 128 elements of
+            // a row in flight at once
+            const int nrow = (ey + 2) * (ez + 2);
+            for (int rr = warp; rr < nrow; rr += kBrickWarps) {   // warp-uniform
+                const int t0 = rr * tx;
+                const int rb = s_tb[t0], re = s_tb[t0 + tx - 1] + s_tn[t0 + tx - 1];
+                const float ay = (float)(rr % (ey + 2)) - hy, az = (float)(rr / (ey + 2)) - hz;   // exact
+                for (int e0 = rb; e0 < re; e0 += 128) {
+                    float4 v[4];
+                    int at[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int e = e0 + 32 * u + lane;
+                        int a = 0;   // the tile cell of element e along the row
+#pragma unroll
+                        for (int c = 1; c < 4; ++c) a += (c < tx && s_tb[t0 + c] <= e) ? 1 : 0;
+                        at[u] = a;
+                        v[u] = e < re ? posq[s_ts[t0 + a] + (e - s_tb[t0 + a])] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int e = e0 + 32 * u + lane;
+                        if (e < re) {
+                            s_t[0][e] = fmaf((float)at[u] - hx, ell.x, v[u].x);
+                            s_t[1][e] = fmaf(ay, ell.y, v[u].y);
+                            s_t[2][e] = fmaf(az, ell.z, v[u].z);
+                            if (!MONO) s_t[NPL - 1][e] = v[u].w;   // type bits
+                        }
+                    }
+                }
+            }
+            // address tables: brick cell cl, stencil cell k
+            for (int t = threadIdx.x; t < nbc * 27; t += blockDim.x) {
+                const int cl = t / 27, k = t - 27 * cl;
+                const int u = cl & sx, v = (cl >> sx) & sy, w = cl >> (sx + sy);
+                const uint32_t dxd = k % 3, dyd = (k / 3) % 3, dzd = k / 9;
+                const int tc = (u + (int)dxd) + tx * (v + (int)dyd) + txy * (w + (int)dzd);
+                // (entry << 2) = 4 j + (dx digit << 28) + (dy digit << 30) mod 2^32
+                s_D[cl][(dzd << 4) | (dyd << 2) | dxd] =
+                    X0 + 4u * (uint32_t)(s_tb[tc] - s_ts[tc]) - (dxd << 28) - (dyd << 30);
+            }
+        }
+        __syncthreads();   // tile and address tables complete
+        float e_acc = 0.f, w_acc = 0.f;   // this thread's energy and virial over the brick
+        for (int ib = 0; ib < npb; ib += kBrickPass) {
+            if (ib + (32 / LJ_TPP) * warp >= npb) break;   // warp-uniform: none of its particles here or later
+            const int slot = ib + grp;
+            const bool act = slot < npb;
+            // its brick cell: the last cl < nbc with s_pc[cl] <= slot (prefix non-decreasing)
+            int cl = (4 < nbc && s_pc[4] <= slot) ? 4 : 0;
+            cl += (cl + 2 < nbc && s_pc[cl + 2] <= slot) ? 2 : 0;
+            cl += (cl + 1 < nbc && s_pc[cl + 1] <= slot) ? 1 : 0;
+            const int p = act ? s_cs[cl] + (slot - s_pc[cl]) : 0;   // no load for an idle group
+            const float4 pi = act ? posq[p] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const uint4* L = reinterpret_cast<const uint4*>(b.nbr + (size_t)K * p) + l4;
+            const uint4 z4 = make_uint4(0u, 0u, 0u, 0u);
+            // the row's first two blocks (inside the row's K >= 16 slots), in
+            // flight with the count; later blocks two ahead
+            uint4 cur = act ? __ldcs(L) : z4;
+            uint4 nx1 = act && K > LJ_ROW_BLOCK ? __ldcs(L + LJ_TPP) : z4;
+            const int cnt = act ? min(b.nbr_count[p], K) : 0;
+            const int nblk = (cnt + LJ_ROW_BLOCK - 1) / LJ_ROW_BLOCK;
+            const int ti = __float_as_int(pi.w);
+            const int lim = cnt - ((nblk - 1) * LJ_ROW_BLOCK + 4 * l4);   // valid entries of the last block
+            PairAcc2 A;
+            A.fx = A.fy = A.fz = A.e = A.w = make_float2(0.f, 0.f);
+            if (tiled) {
+                const int u = cl & sx, v = (cl >> sx) & sy, w = cl >> (sx + sy);
+                // p_i in the brick frame: one rounding
+                const float px = fmaf((float)(u + 1) - hx, ell.x, pi.x), py = fmaf((float)(v + 1) - hy, ell.y, pi.y),
+                            pz = fmaf((float)(w + 1) - hz, ell.z, pi.z);
+                const float2 nx = make_float2(-px, -px), ny = make_float2(-py, -py), nz = make_float2(-pz, -pz);
+                const uint32_t* D = s_D[cl];
+                for (int blk = 0; blk + 1 < nblk; ++blk) {
+                    const uint4 nx2 = blk + 2 < nblk ? __ldcs(L + (blk + 2) * LJ_TPP) : z4;   // two ahead
+                    tile_pair2<MONO, ENERGY, PL>(tile_addr(cur.x, D), tile_addr(cur.y, D), nx, ny, nz, ti, nt, s_lj,
+                                                 s_rc2, s_esh, mlj, mrc2, mesh, A);
+                    tile_pair2<MONO, ENERGY, PL>(tile_addr(cur.z, D), tile_addr(cur.w, D), nx, ny, nz, ti, nt, s_lj,
+                                                 s_rc2, s_esh, mlj, mrc2, mesh, A);
+                    cur = nx1;
+                    nx1 = nx2;
+                }
+                if (nblk > 0) {   // the last block: entries past the count name the sentinel
+                    const uint32_t a0 = lim > 0 ? tile_addr(cur.x, D) : SENT;
+                    const uint32_t a1 = lim > 1 ? tile_addr(cur.y, D) : SENT;
+                    const uint32_t a2 = lim > 2 ? tile_addr(cur.z, D) : SENT;
+                    const uint32_t a3 = lim > 3 ? tile_addr(cur.w, D) : SENT;
+                    tile_pair2<MONO, ENERGY, PL>(a0, a1, nx, ny, nz, ti, nt, s_lj, s_rc2, s_esh, mlj, mrc2, mesh, A);
+                    tile_pair2<MONO, ENERGY, PL>(a2, a3, nx, ny, nz, ti, nt, s_lj, s_rc2, s_esh, mlj, mrc2, mesh, A);
+                }
+            } else {   // neighbourhood larger than the tile: gathers from global memory
+                float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f, vir = 0.f;
+                for (int blk = 0; blk < nblk; ++blk) {
+                    const bool last = blk + 1 == nblk;
+                    const uint4 nx2 = blk + 2 < nblk ? __ldcs(L + (blk + 2) * LJ_TPP) : z4;
+                    uint32_t q[4] = {cur.x, cur.y, cur.z, cur.w};
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const unsigned ek = (!last || lim > k) ? q[k] : sent_ent;
+                        const float4 pj = __ldg(posq + (ek & LJ_IDX_MASK));
+                        pair_f32<MONO, ENERGY>(ek, pj, pi, ti, ell, s_lj, s_rc2, s_esh, nt, mlj, mrc2, mesh, fx, fy,
+                                               fz, e, vir);
+                    }
+                    cur = nx1;
+                    nx1 = nx2;
+                }
+                // d_ij orientation here: stored negated like the tile path's sums
+                A.fx = make_float2(-fx, 0.f);
+                A.fy = make_float2(-fy, 0.f);
+                A.fz = make_float2(-fz, 0.f);
+                A.e = make_float2(e, 0.f);
+                A.w = make_float2(vir, 0.f);
+            }
+            float fx = A.fx.x + A.fx.y, fy = A.fy.x + A.fy.y, fz = A.fz.x + A.fz.y;
+            if (ENERGY) {   // idle groups hold zeros
+                e_acc += A.e.x + A.e.y;
+                w_acc += A.w.x + A.w.y;
+            }
+#pragma unroll
+            for (int o = LJ_TPP / 2; o > 0; o >>= 1) {
+                fx += __shfl_xor_sync(FULL, fx, o);
+                fy += __shfl_xor_sync(FULL, fy, o);
+                fz += __shfl_xor_sync(FULL, fz, o);
+            }
+            if (act && l4 == 0) {
+                b.force4[p] = make_float4(-fx, -fy, -fz, 0.f);
+                if (!isfinite(fx + fy + fz)) atomicOr(&b.err[0], LJ_ERRBIT_NONFINITE);
+            }
+        }
+        if (ENERGY) {
+            // one (E_pot, W) share per warp and brick, written for every brick
+            // (zeros where the warp had no particle): the warp sum in
+            // double-single, stored as the (hi, lo) pair, halved exactly
+            // (each pair is in two rows of a full list)
+            const float2 de = warp_sum_ds2(e_acc), dw = warp_sum_ds2(w_acc);
+            if (lane == 0)
+                reinterpret_cast<float4*>(b.part_f)[(size_t)bi * kBrickWarps + warp] =
+                    make_float4(0.5f * de.x, 0.5f * de.y, 0.5f * dw.x, 0.5f * dw.y);
+        }
+        __syncthreads();   // the tile is free for the next brick
+    }
+}
+
 // FP64 pair force (MD_PREC_FP64), one thread per particle over 128-particle
 // chunks, FP64 cell-relative offsets gathered from global memory.
 template <bool ENERGY>
@@ -607,19 +961,27 @@ __global__ void __launch_bounds__(LJ_THERMO_THREADS) k_thermo(BoxDev b, double* 
         double e = 0.0, w = 0.0, k = 0.0;
         const int pf = b.pf_stride;
         const double2* sh = reinterpret_cast<const double2*>(b.part_f);   // (E_pot, W) shares
+        // the item's (E_pot, W) shares: those of its chunks, or, from the
+        // tiled force kernel, those of its share of the replica's bricks
+        int s0 = t.y * pf, s1 = t.z * pf;
+        if (b.force_tiles) {
+            const int q = it - R.ti_off;
+            s0 = (R.brick_off + (int)(((long long)q * R.nbrick) / R.nti)) * pf;
+            s1 = (R.brick_off + (int)(((long long)(q + 1) * R.nbrick) / R.nti)) * pf;
+        }
         // four independent loads in flight per thread, then their sums
         const int nt4 = 4 * (int)blockDim.x;
-        for (int c0 = t.y * pf; c0 < t.z * pf; c0 += nt4) {
+        for (int c0 = s0; c0 < s1; c0 += nt4) {
             double2 v[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int c = c0 + u * (int)blockDim.x + (int)threadIdx.x;
                 if (b.pf_ds) {   // (hi, lo) float pairs
-                    const float4 f = c < t.z * pf ? reinterpret_cast<const float4*>(b.part_f)[c]
-                                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const float4 f = c < s1 ? reinterpret_cast<const float4*>(b.part_f)[c]
+                                            : make_float4(0.f, 0.f, 0.f, 0.f);
                     v[u] = make_double2((double)f.x + (double)f.y, (double)f.z + (double)f.w);
                 } else {
-                    v[u] = c < t.z * pf ? sh[c] : make_double2(0.0, 0.0);
+                    v[u] = c < s1 ? sh[c] : make_double2(0.0, 0.0);
                 }
             }
 #pragma unroll
@@ -690,6 +1052,14 @@ cudaError_t launch_force(const BoxDev& b, int energy, Launch l)
     if (b.prec == 2) {
         if (energy) k_force_f64<true><<<l.grid, LJ_F64_THREADS, 0, l.s>>>(b);
         else k_force_f64<false><<<l.grid, LJ_F64_THREADS, 0, l.s>>>(b);
+    } else if (b.force_tiles) {
+        if (b.nt == 1) {
+            if (energy) k_force_tile_f32<true, true><<<l.grid, LJ_BRICK_THREADS, 0, l.s>>>(b);
+            else k_force_tile_f32<true, false><<<l.grid, LJ_BRICK_THREADS, 0, l.s>>>(b);
+        } else {
+            if (energy) k_force_tile_f32<false, true><<<l.grid, LJ_BRICK_THREADS, 0, l.s>>>(b);
+            else k_force_tile_f32<false, false><<<l.grid, LJ_BRICK_THREADS, 0, l.s>>>(b);
+        }
     } else if (b.nt == 1 && b.nrep == 1) {
         if (energy) k_force_f32<true, true, true><<<l.grid, LJ_FORCE_THREADS, 0, l.s>>>(b);
         else k_force_f32<true, false, true><<<l.grid, LJ_FORCE_THREADS, 0, l.s>>>(b);
@@ -701,6 +1071,22 @@ cudaError_t launch_force(const BoxDev& b, int energy, Launch l)
         else k_force_f32<false, false, false><<<l.grid, LJ_FORCE_THREADS, 0, l.s>>>(b);
     }
     return cudaGetLastError();
+}
+
+// Resident blocks per SM of the tiled force kernel (its persistent grid).
+int force_tile_blocks_per_sm(int mono)
+{
+    static int occ[2] = {0, 0};
+    int& o = occ[mono ? 1 : 0];
+    if (o == 0) {
+        int v = 0;
+        cudaError_t e = mono ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_force_tile_f32<true, true>,
+                                                                             LJ_BRICK_THREADS, 0)
+                             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_force_tile_f32<false, true>,
+                                                                             LJ_BRICK_THREADS, 0);
+        o = (e == cudaSuccess && v > 0) ? v : 4;
+    }
+    return o;
 }
 
 cudaError_t launch_thermo(const BoxDev& b, double* out, int with_kin, Launch l)

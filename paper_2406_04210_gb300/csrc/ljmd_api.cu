@@ -92,6 +92,9 @@ struct md_box {
     int4* d_seg = nullptr;
     LJDev* d_lj = nullptr;
     int4* d_tiles = nullptr;
+    std::vector<int4> bricks;  // work items of the tiled force kernel: (replica, first cell x, y, z)
+    size_t pf_cap = 0;         // doubles of d.part_f
+    int4* d_brick = nullptr;
     int* d_tile_sum = nullptr;
     int* d_type_user = nullptr;
     double* d_thermo = nullptr;
@@ -116,6 +119,7 @@ struct md_box {
     bool autofit = false;      // fit the capacity after the next full build
     double cell_scale = 1.0;   // cell edge / list radius (>= 1)
     int list_kernel = 0;       // MD_LIST_AUTO / MD_LIST_QUADS / MD_LIST_LANES
+    int force_kernel = 0;      // MD_FORCE_AUTO / MD_FORCE_CHUNKS / MD_FORCE_TILES
     int order = 0;             // order inside a cell (MD_ORDER_*)
     int force_per_sm = 0;      // 0 = automatic (tuning)
     int list_per_sm = 0;
@@ -249,8 +253,26 @@ void invalidate_graphs(md_box* b)
 Launch lch(md_box* b) { return Launch{std::max(1, std::min((int)b->d.nchunk, b->nsm * 12)), LJ_CHUNK, b->stream}; }
 Launch lthermo(md_box* b) { return Launch{std::max(1, std::min(b->d.ntitem, b->nsm * 8)), LJ_THERMO_THREADS, b->stream}; }
 Launch lcell(md_box* b) { return Launch{std::max(1, std::min((b->d.ncell + 7) / 8, b->nsm * 8)), 256, b->stream}; }
+// The FP32 list-form force kernel and the layout of its (E_pot, W) shares:
+// the chunk kernel unless the tiled one is asked for (or chosen by
+// md_autotune).  The FP32 list
+// kernels leave one double-single share per warp and chunk (chunk kernel)
+// or brick (tiled kernel, LJ_BRICK_WARPS = LJ_FORCE_WARPS), the FP64 one an
+// FP64 share per warp and chunk, the all-pairs kernels one per chunk.
+void apply_force_kernel(md_box* b)
+{
+    const bool list32 = !b->all_pairs && b->prec != MD_PREC_FP64;
+    const bool tiles = list32 && b->force_kernel == MD_FORCE_TILES;
+    b->d.force_tiles = tiles ? 1 : 0;
+    b->d.pf_stride = b->all_pairs ? 1 : b->prec == MD_PREC_FP64 ? LJ_F64_WARPS : LJ_FORCE_WARPS;
+    b->d.pf_ds = list32 ? 1 : 0;
+}
+
 Launch lforce(md_box* b)
 {
+    if (b->d.force_tiles)   // persistent: the resident blocks, bricks handed out in a grid stride
+        return Launch{std::max(1, std::min((int)b->d.nbrick, b->nsm * force_tile_blocks_per_sm(b->d.nt == 1))), 0,
+                      b->stream};
     int per_sm = b->force_per_sm > 0 ? b->force_per_sm : (b->prec == 2 ? 12 : 6);
     const int items = b->all_pairs ? b->d.nchunk * std::max(1, b->d.ap_js) : b->d.nchunk;
     return Launch{std::max(1, std::min(items, b->nsm * per_sm)), 0, b->stream};
@@ -481,6 +503,7 @@ md_status make_grid(md_box* b)
     BoxDev& d = b->d;
     invalidate_graphs(b);
     b->tiles.clear();
+    b->bricks.clear();
     int cell_off = 0;
     double maxdens = 0.0;
     for (int r = 0; r < b->nrep; ++r) {
@@ -494,6 +517,15 @@ md_status make_grid(md_box* b)
         }
         R.cell_off = cell_off;
         R.ncell = R.nc[0] * R.nc[1] * R.nc[2];
+        // bricks of the tiled force kernel: 2 cells along an axis where the
+        // brick-centre frame keeps tile coordinates below 8 (2 ell + drift),
+        // else 1; x fastest, so that neighbouring blocks share tile cells in L2
+        for (int c = 0; c < 3; ++c) R.br[c] = (R.nc[c] >= 2 && R.ellf[c] < 3.9f) ? 2 : 1;
+        R.brick_off = (int)b->bricks.size();
+        for (int z = 0; z < R.nc[2]; z += R.br[2])
+            for (int y = 0; y < R.nc[1]; y += R.br[1])
+                for (int x = 0; x < R.nc[0]; x += R.br[0]) b->bricks.push_back(make_int4(r, x, y, z));
+        R.nbrick = (int)b->bricks.size() - R.brick_off;
         int first_tile = (int)b->tiles.size();
         for (int c0 = 0; c0 < R.ncell; c0 += ljmd_scan_tile_cells())
             b->tiles.push_back(make_int4(r, cell_off + c0,
@@ -511,6 +543,8 @@ md_status make_grid(md_box* b)
     dev_release(b, d.cell_end);
     dev_release(b, (void*)d.cell_rep);
     dev_release(b, b->d_tiles);
+    dev_release(b, b->d_brick);
+    b->d_brick = nullptr;
     dev_release(b, b->d_tile_sum);
     d.cell_count = d.cell_start = d.cell_end = nullptr;
     d.cell_rep = nullptr;
@@ -531,6 +565,22 @@ md_status make_grid(md_box* b)
     CKS(dev_alloc(b, &b->d_tile_sum, b->tiles.size()));
     CK(b, cudaMemcpyAsync(b->d_tiles, b->tiles.data(), sizeof(int4) * b->tiles.size(),
                           cudaMemcpyHostToDevice, b->stream));
+    CKS(dev_alloc(b, &b->d_brick, b->bricks.size(), false));
+    CK(b, cudaMemcpyAsync(b->d_brick, b->bricks.data(), sizeof(int4) * b->bricks.size(),
+                          cudaMemcpyHostToDevice, b->stream));
+    CK(b, cudaStreamSynchronize(b->stream));   // `bricks` may change before the copy would run
+    d.brick = b->d_brick;
+    d.nbrick = (int)b->bricks.size();
+    {   // (E_pot, W) shares: 8 per chunk or per brick
+        const size_t need = 2 * LJ_FORCE_WARPS * std::max<size_t>(1, std::max(b->chunks.size(), b->bricks.size()));
+        if (need > b->pf_cap) {
+            dev_release(b, d.part_f);
+            d.part_f = nullptr;
+            b->pf_cap = 0;
+            CKS(dev_alloc(b, &d.part_f, need));
+            b->pf_cap = need;
+        }
+    }
     CKS(make_segments(b, false));
     // list capacity: expected neighbours at the densest replica, +30 %
     double expect = b->all_pairs ? 0.0 : maxdens * 4.18879020478639 * b->rl * b->rl * b->rl;
@@ -1055,9 +1105,11 @@ md_status md_batch_create(md_box** out, int32_t nrep, const int64_t* n, const do
         CKS(dev_alloc(b, &d.err, 4));
         CKS(dev_alloc(b, &b->d_cond_runs, 1));
         CKS(dev_alloc(b, &d.part_k, LJ_KIN_WARPS * std::max<size_t>(1, b->chunks.size())));
-        CKS(dev_alloc(b, &d.part_f, 2 * LJ_FORCE_WARPS * std::max<size_t>(1, b->chunks.size())));
-        d.pf_stride = prec == MD_PREC_FP64 ? LJ_F64_WARPS : LJ_FORCE_WARPS;
-        d.pf_ds = prec == MD_PREC_FP64 ? 0 : 1;
+        // (E_pot, W) shares, 8 per chunk (chunk kernel) or brick (tiled
+        // kernel; make_grid grows the array with the bricks)
+        b->pf_cap = 2 * LJ_FORCE_WARPS * std::max<size_t>(1, b->chunks.size());
+        CKS(dev_alloc(b, &d.part_f, b->pf_cap));
+        apply_force_kernel(b);
         CKS(dev_alloc(b, &b->d_type_user, std::max<int64_t>(1, ntot)));
         CK(b, cudaMemcpyAsync(b->d_rep, b->reps.data(), sizeof(RepDev) * b->reps.size(),
                               cudaMemcpyHostToDevice, b->stream));
@@ -1152,9 +1204,7 @@ md_status md_set_lj(md_box* b, int32_t ntypes, const double* eps, const double* 
     bool grid_changes = !b->lj_set || rl != b->rl || all_pairs != b->all_pairs;
     b->all_pairs = all_pairs;
     b->d.all_pairs = all_pairs ? 1 : 0;
-    // (E_pot, W) shares per chunk: the list kernels leave one per warp
-    b->d.pf_stride = all_pairs ? 1 : b->prec == MD_PREC_FP64 ? LJ_F64_WARPS : LJ_FORCE_WARPS;
-    b->d.pf_ds = (!all_pairs && b->prec != MD_PREC_FP64) ? 1 : 0;   // the FP32 list kernel's shares
+    apply_force_kernel(b);   // the force kernel and its (E_pot, W) shares
     if (all_pairs && !b->d.ap_cnt) {
         // j slices per chunk: enough work items to fill the GPU, each slice
         // at least ~128 particles
@@ -1771,11 +1821,13 @@ md_status md_autotune(md_box* b, int32_t reps, int32_t t[4])
     if (!b || !b->lj_set || reps < 1) return fail(b, MD_ERR_ARG, "md_autotune: md_set_lj not called");
     if (b->all_pairs) return fail(b, MD_ERR_ARG, "md_autotune: not in the all-pairs form");
     CKS(enter(b));
-    // pair-force grid: blocks per SM
+    // pair-force grid of the chunk kernel: blocks per SM (the tiled kernel
+    // runs its resident blocks)
     const int fcand[] = {2, 3, 4, 6, 8, 12, 16, 24, 32};
-    int best_f = 6;
+    int best_f = b->force_per_sm > 0 ? b->force_per_sm : 6;
     float best_ft = 1e30f;
     for (int c : fcand) {
+        if (b->d.force_tiles) break;
         b->force_per_sm = c;
         float ms;
         CKS(time_launches(b, reps, [&]() -> md_status { return enqueue_force(b, 1, nullptr); }, &ms));
@@ -1902,6 +1954,21 @@ md_status md_autotune(md_box* b, int32_t reps, int32_t t[4])
         invalidate_graphs(b);
         CKS(full_rebuild(b));
     }
+    // the FP32 list-form force kernel, unless the caller fixed it: both timed
+    // at the chosen layout, the faster kept (md_get_force_kernel reads it)
+    if (b->force_kernel == MD_FORCE_AUTO && !b->all_pairs && b->prec != MD_PREC_FP64) {
+        const int kinds[2] = {MD_FORCE_CHUNKS, MD_FORCE_TILES};
+        float tk[2] = {1e30f, 1e30f};
+        for (int i = 0; i < 2; ++i) {
+            b->force_kernel = kinds[i];
+            apply_force_kernel(b);
+            CKS(time_launches(b, reps, [&]() -> md_status { return enqueue_force(b, 1, nullptr); }, &tk[i]));
+        }
+        b->force_kernel = tk[1] < tk[0] ? MD_FORCE_TILES : MD_FORCE_CHUNKS;
+        apply_force_kernel(b);
+        invalidate_graphs(b);
+        CKS(enqueue_force(b, 1, nullptr));   // the box's forces from the kept kernel
+    }
     CKS(leave(b));
     return md_get_tuning(b, t);
 }
@@ -1931,6 +1998,25 @@ md_status md_set_list_kernel(md_box* b, int32_t kind)
         b->list_kernel = kind;
         invalidate_graphs(b);
     }
+    return MD_OK;
+}
+
+md_status md_set_force_kernel(md_box* b, int32_t kind)
+{
+    if (!b || kind < MD_FORCE_AUTO || kind > MD_FORCE_TILES)
+        return fail(b, MD_ERR_ARG, "md_set_force_kernel: kind must be 0, 1 or 2");
+    if (kind != b->force_kernel) {
+        b->force_kernel = kind;
+        apply_force_kernel(b);
+        invalidate_graphs(b);
+    }
+    return MD_OK;
+}
+
+md_status md_get_force_kernel(md_box* b, int32_t* kind)
+{
+    if (!b || !kind) return MD_ERR_ARG;
+    *kind = b->force_kernel;
     return MD_OK;
 }
 
@@ -1995,8 +2081,11 @@ double* g_noalloc_dev[kMaxDevices] = {};   // device address of the array, per d
 extern "C" md_status md_force_noalloc(md_box* b, double* force_out, double* epot, double* virial)
 {
     if (!b) return MD_ERR_ARG;
+    // the chunk kernels always (their shares are per warp, not per particle)
+    BoxDev v = b->d;
+    v.force_tiles = 0;   // same share layout per chunk as the FP32 list kernels
     const size_t nchunk = b->chunks.size();
-    const size_t nshare = 2 * (size_t)b->d.pf_stride * nchunk;   // (E_pot, W) shares
+    const size_t nshare = 2 * (size_t)v.pf_stride * nchunk;   // (E_pot, W) shares
     const size_t need = nshare + 4 * (size_t)b->nrep;
     if (need > (size_t)LJMD_NOALLOC_DOUBLES) {
         char msg[240];
@@ -2023,11 +2112,15 @@ extern "C" md_status md_force_noalloc(md_box* b, double* force_out, double* epot
         scratch = g_noalloc_dev[b->device];
     }
     CKS(enter(b));
-    BoxDev v = b->d;
     v.part_f = scratch;                       // every chunk's shares are overwritten
     double* th = scratch + nshare;            // nrep x (E_pot, E_kin, W, T), overwritten
     CKS(clear_err(b));
-    CK(b, launch_force(v, 1, lforce(b)));
+    Launch lf = lforce(b);
+    if (b->d.force_tiles) {   // the chunk kernel's grid
+        const int per_sm = b->force_per_sm > 0 ? b->force_per_sm : 6;
+        lf.grid = std::max(1, std::min((int)v.nchunk, b->nsm * per_sm));
+    }
+    CK(b, launch_force(v, 1, lf));
     CK(b, launch_thermo(v, th, 0, lthermo(b)));
     if (force_out && b->ntot > 0) CK(b, launch_force_out(b->d, force_out, lch(b)));
     if (epot)

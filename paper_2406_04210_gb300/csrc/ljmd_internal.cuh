@@ -55,6 +55,9 @@
 #define LJ_FLAT_MAX 1024       // candidates of one cell's 27-cell neighbourhood (list build)
 #define LJ_LIST_SMEM (32 * 1024)   // bytes of a segment's list staged in smem
 #define LJ_ROW_BLOCK 16        // the FP32 force kernel reads list rows in blocks of this many entries
+#define LJ_BRICK_THREADS 256   // threads of the tiled FP32 pair-force kernel (LJ_TPP per particle)
+#define LJ_BRICK_WARPS (LJ_BRICK_THREADS / 32)   // its (E_pot, W) shares per brick
+#define LJ_BRICK_TILE 2048     // particles of a brick's neighbourhood staged in shared memory
 // In a row's last block the FP32 force kernel replaces the entries past the
 // count by slot np, one past the last particle: posq[np] holds this offset on
 // every axis, so that the pair distance, squared, stays finite (~3e30) and
@@ -88,6 +91,8 @@ struct RepDev {
     int ti_off, nti;           // energy-reduction items of this replica
     int seg_off, nseg;         // segments of this replica
     int S;                     // cells per segment (along x)
+    int br[3];                 // brick edge in cells (1 or 2) of the tiled force kernel
+    int brick_off, nbrick;     // its bricks of this replica
 };
 
 // Slot ranges of a segment's tile: piece q (0..17) is row rr = q/2 with
@@ -190,6 +195,9 @@ struct BoxDev {
     const double* tstat_T;
     long long* step_ctr;       // steps since md_set_thermostat (device word)
     int all_pairs;             // every cutoff infinite: forces over all pairs, no lists
+    int force_tiles;           // FP32 list forces by the tiled kernel (k_force_tile_f32)
+    const int4* brick;         // its work items: (replica, first cell x, y, z) of bricks of up to
+    int nbrick;                // rep.br[0] x br[1] x br[2] cells
     int order;                 // order inside a cell: 0 z runs (LJ_ORDER_ZRUN), 1 Morton sub-cells
     int ap_js;                 // all pairs: slices of the j range per chunk
     float4* ap_part;           // [slice][slot] partial FP32 forces
@@ -200,7 +208,8 @@ struct BoxDev {
     double* part_f;            // [(chunk*pf_stride + q)*2 + 0] = E_pot share, [+1] = W share
     int pf_stride;             // (E_pot, W) shares per chunk: one per warp of the list kernels, 1 for all pairs
     int pf_ds;                 // 1: each share is a double-single pair (hi, lo floats in the double's
-                               // 8 bytes: the FP32 list kernel), 0: a double
+                               // 8 bytes: the FP32 list kernels), 0: a double; the tiled kernel
+                               // leaves pf_stride shares per brick instead of per chunk
     double* part_k;            // [chunk*LJ_KIN_WARPS + warp] = E_kin share
     double* part_t;            // [item*3 + 0..2] = E_pot, W, E_kin of a reduction item
     unsigned* tcount;          // per replica: reduction items finished (last one resets)
@@ -521,6 +530,7 @@ cudaError_t launch_set_rebuild_cond(cudaGraphConditionalHandle h, const BoxDev& 
 // k_force.cu
 cudaError_t launch_force(const BoxDev& b, int energy, Launch l);
 cudaError_t launch_thermo(const BoxDev& b, double* out, int with_kin, Launch l);
+int force_tile_blocks_per_sm(int mono);   // resident blocks of the tiled force kernel
 
 // k_adjoint.cu
 cudaError_t launch_adj_pre(const BoxDev& b, double* lx, double* lv, const double* g, float4* u_slot, double h,

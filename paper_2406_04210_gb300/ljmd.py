@@ -30,7 +30,8 @@ EXPORTS = ["md_set_allocator", "md_batch_create", "md_box_create", "md_box_destr
            "md_set_lj", "md_neighbour_update", "md_force", "md_integrate", "md_adjoint",
            "md_get_state", "md_set_state", "md_get_nlist", "md_get_info", "md_set_tuning",
            "md_get_tuning", "md_autotune", "md_set_layout", "md_get_layout",
-           "md_set_list_kernel", "md_get_list_kernel", "md_set_graph_conditional",
+           "md_set_list_kernel", "md_get_list_kernel", "md_set_force_kernel",
+           "md_get_force_kernel", "md_set_graph_conditional",
            "md_get_graph_conditional",
            "md_set_profiling", "md_get_profile", "md_pair_hist", "md_force_noalloc",
            "md_set_thermostat",
@@ -100,6 +101,8 @@ def load(path: str | None = None):
         L.md_get_layout.argtypes = [vp, vp, vp]
         L.md_set_list_kernel.argtypes = [vp, i32]
         L.md_get_list_kernel.argtypes = [vp, vp]
+        L.md_set_force_kernel.argtypes = [vp, i32]
+        L.md_get_force_kernel.argtypes = [vp, vp]
         L.md_set_graph_conditional.argtypes = [vp, i32]
         L.md_get_graph_conditional.argtypes = [vp, vp]
         L.md_set_profiling.argtypes = [vp, i32]
@@ -368,6 +371,20 @@ class Box:
     def list_kernel(self, kind):
         self._check(self._lib.md_set_list_kernel(self._h, self.LIST_KERNELS[kind]), "md_set_list_kernel")
 
+    FORCE_KERNELS = {"auto": 0, "chunks": 1, "tiles": 2}
+
+    @property
+    def force_kernel(self):
+        """FP32 list-form force kernel: "auto", "chunks" or "tiles"
+        (md_set_force_kernel)."""
+        k = ctypes.c_int32()
+        self._check(self._lib.md_get_force_kernel(self._h, ctypes.byref(k)), "md_get_force_kernel")
+        return {v: n for n, v in self.FORCE_KERNELS.items()}[k.value]
+
+    @force_kernel.setter
+    def force_kernel(self, kind):
+        self._check(self._lib.md_set_force_kernel(self._h, self.FORCE_KERNELS[kind]), "md_set_force_kernel")
+
     @property
     def graph_conditional(self):
         """True when step graphs hold the list update as a conditional node
@@ -409,6 +426,9 @@ class Box:
                 kind = ent.pop("list_kernel", None)
                 if kind is not None:
                     self.list_kernel = kind
+                fkind = ent.pop("force_kernel", None)
+                if fkind is not None:
+                    self.force_kernel = fkind
                 self.set_tuning(**ent)
                 if lay:
                     self.set_layout(**lay)
@@ -418,6 +438,7 @@ class Box:
         res = dict(zip(self.TUNING, (int(x) for x in t)))
         res.update(self.layout())
         res["list_kernel"] = self.list_kernel
+        res["force_kernel"] = self.force_kernel
         if cache and path:
             try:
                 os.makedirs(os.path.dirname(path), exist_ok=True)

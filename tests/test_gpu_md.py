@@ -356,6 +356,7 @@ def test_autotune_keeps_results(ljmd):
     assert 1 <= t["force_blocks_per_sm"] <= 32 and 1 <= t["list_blocks_per_sm"] <= 32
     assert 1 <= t["segment_cells"] <= 16
     assert t["list_kernel"] in ("lanes", "quads") and b.list_kernel == t["list_kernel"]
+    assert t["force_kernel"] in ("chunks", "tiles") and b.force_kernel == t["force_kernel"]
     f1, e1, _ = b.force()
     S = pair_scale(s.box, s.pos, _lj(s))
     assert (np.linalg.norm(f1 - f0, axis=1) / S).max() <= 1e-5
