@@ -328,21 +328,37 @@ __device__ __forceinline__ void tile_pair2(uint32_t a0, uint32_t a1, const float
 __device__ __forceinline__ uint32_t tile_addr(uint32_t e, const uint32_t* D) { return (e << 2) + D[e >> 26]; }
 
 static_assert(LJ_BRICK_WARPS == LJ_FORCE_WARPS, "per-brick shares in the chunk kernel's share stride");
-constexpr int kBrickThreads = LJ_BRICK_THREADS;
-constexpr int kBrickWarps = kBrickThreads / 32;
-constexpr int kBrickPass = kBrickThreads / LJ_TPP;   // particles per block pass
+constexpr int kBrickThreads = LJ_BRICK_THREADS;          // consumer threads
+constexpr int kBrickWarps = kBrickThreads / 32;          // consumer warps (the producer is warp kBrickWarps)
+constexpr int kBrickPass = kBrickThreads / LJ_TPP;       // particles per consumer pass
+
+__device__ __forceinline__ void mbar_arrive1(unsigned long long* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Dynamic shared memory of k_force_tile_f32: two buffers of NPL planes.
+constexpr size_t tile_buf_bytes(bool mono) { return (size_t)(mono ? 3 : 4) * (LJ_BRICK_TILE + 1) * 4; }
+
+// Producer warp kBrickWarps stages brick k + 1 (tile planes, brick-cell
+// tables, address tables) into one buffer while the consumer warps compute
+// brick k from the other; full[buf] (32 arrivals, the producer's lanes) and
+// empty[buf] (kBrickThreads arrivals, the consumers) hand the buffers over.
+// Every wait is bounded: on a timeout the warp records LJ_ERRBIT_TIMEOUT and
+// leaves, and the others then time out in turn.
 template <bool MONO, bool ENERGY>
-__global__ void __launch_bounds__(LJ_BRICK_THREADS, 5) k_force_tile_f32(BoxDev b)
+__global__ void __launch_bounds__(LJ_BRICK_THREADS + 32, 4) k_force_tile_f32(BoxDev b)
 {
     constexpr int T = LJ_BRICK_TILE;
     constexpr int NPL = MONO ? 3 : 4;   // x, y, z (and type) planes
     constexpr int PL = (T + 1) * 4;     // bytes per plane; element T of each is the sentinel
+    constexpr int BUF = NPL * PL;       // bytes per buffer
     constexpr unsigned FULL = 0xffffffffu;
-    __shared__ __align__(16) float s_t[NPL][T + 1];
-    __shared__ uint32_t s_D[8][64];     // per brick cell and stencil-digit code: tile address term
-    __shared__ int s_tb[64], s_ts[64], s_tn[64];   // tile cells: base in the tile, first slot, particles
-    __shared__ int s_pc[9], s_cs[8];    // brick cells: particle prefix, first slot
-    __shared__ int s_tot;
+    extern __shared__ __align__(16) float s_dyn[];   // [2][NPL][T + 1]
+    __shared__ uint32_t s_D[2][8][64];  // per buffer, brick cell and stencil-digit code: tile address term
+    __shared__ int s_pc[2][9], s_cs[2][8], s_nb[2], s_tiled[2];   // per buffer: brick cells, particles
+    __shared__ int s_tb[64], s_ts[64], s_tn[64];                  // producer: tile cells
+    __shared__ unsigned long long s_full[2], s_empty[2];
     __shared__ float4 s_lj[MONO ? 1 : LJ_MAXT * LJ_MAXT];
     __shared__ float s_rc2[MONO ? 1 : LJ_MAXT * LJ_MAXT];
     __shared__ float s_esh[MONO ? 1 : LJ_MAXT * LJ_MAXT];
@@ -355,38 +371,48 @@ __global__ void __launch_bounds__(LJ_BRICK_THREADS, 5) k_force_tile_f32(BoxDev b
             s_esh[k] = lj->shift[k];
         }
     }
-    if (threadIdx.x < NPL) s_t[threadIdx.x][T] = threadIdx.x < 3 ? LJ_SENTINEL_OFF : 0.f;   // type 0
-    const uint32_t X0 = (uint32_t)__cvta_generic_to_shared(&s_t[0][0]);
-    const uint32_t SENT = X0 + 4u * (uint32_t)T;
+    if (threadIdx.x < 2 * NPL) {   // sentinels: far offsets, type 0
+        const int q = threadIdx.x % NPL;
+        s_dyn[(threadIdx.x / NPL) * NPL * (T + 1) + q * (T + 1) + T] = q < 3 ? LJ_SENTINEL_OFF : 0.f;
+    }
+    if (threadIdx.x == 0) {
+        mbar_init(&s_full[0], 32);
+        mbar_init(&s_full[1], 32);
+        mbar_init(&s_empty[0], kBrickThreads);
+        mbar_init(&s_empty[1], kBrickThreads);
+    }
+    __syncthreads();   // the block's only barrier: the roles part here
+    const uint32_t X0 = (uint32_t)__cvta_generic_to_shared(s_dyn);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int grp = threadIdx.x / LJ_TPP, l4 = threadIdx.x % LJ_TPP;
-    const int K = b.K;
     const float4* __restrict__ posq = b.posq;
-    const float4 mlj = b.c1;
-    const float mrc2 = b.rc2_1, mesh = b.esh_1;
-    const unsigned sent_ent = entry_make(13, b.np);
-    for (int bi = blockIdx.x; bi < b.nbrick; bi += gridDim.x) {
-        const int4 B = b.brick[bi];
-        const int r = B.x;
-        const RepDev& R = b.rep[r];
-        const int ex = min(R.br[0], R.nc[0] - B.y), ey = min(R.br[1], R.nc[1] - B.z),
-                  ez = min(R.br[2], R.nc[2] - B.w);
-        const int tx = ex + 2, txy = tx * (ey + 2), ntc = txy * (ez + 2), nbc = ex * ey * ez;
-        // brick cell cl = u + ex (v + ey w), extents 1 or 2: u = cl & sx,
-        // v = (cl >> sx) & sy, w = cl >> (sx + sy)
-        const int sx = ex - 1, sy = ey - 1;
-        const float3 ell = make_float3(R.ellf[0], R.ellf[1], R.ellf[2]);
-        // tile coordinate t along an axis (brick cell u is t = u + 1): its
-        // offset in cells from the brick centre, t - (extent + 1) / 2
-        const float hx = 0.5f * (float)(ex + 1), hy = 0.5f * (float)(ey + 1), hz = 0.5f * (float)(ez + 1);
-        if (threadIdx.x == 0) {
-            if (bi == 0) *b.any_req = 0;   // the list update of this step has run
-            if (B.y == 0 && B.z == 0 && B.w == 0) {   // the replica's first brick: clear its rebuild triggers
-                b.disp_max[r] = 0u;
-                b.rebuild_req[r] = 0;
+
+    if (warp == kBrickWarps) {
+        // ---------------- producer ----------------
+        int k = 0;
+        for (int bi = blockIdx.x; bi < b.nbrick; bi += gridDim.x, ++k) {
+            const int buf = k & 1;
+            if (k >= 2 && !mbar_wait(&s_empty[buf], ((k >> 1) - 1) & 1)) {
+                if (lane == 0) atomicOr(&b.err[0], LJ_ERRBIT_TIMEOUT);
+                return;
             }
-        }
-        if (warp == 0) {
+            const int4 B = b.brick[bi];
+            const int r = B.x;
+            const RepDev& R = b.rep[r];
+            if (lane == 0) {
+                if (bi == 0) *b.any_req = 0;   // the list update of this step has run
+                if (B.y == 0 && B.z == 0 && B.w == 0) {   // the replica's first brick: clear its rebuild triggers
+                    b.disp_max[r] = 0u;
+                    b.rebuild_req[r] = 0;
+                }
+            }
+            const int ex = min(R.br[0], R.nc[0] - B.y), ey = min(R.br[1], R.nc[1] - B.z),
+                      ez = min(R.br[2], R.nc[2] - B.w);
+            const int tx = ex + 2, txy = tx * (ey + 2), ntc = txy * (ez + 2), nbc = ex * ey * ez;
+            const int sx = ex - 1, sy = ey - 1;   // brick cell cl = u + ex (v + ey w): u = cl & sx, ...
+            const float3 ell = make_float3(R.ellf[0], R.ellf[1], R.ellf[2]);
+            // tile coordinate t along an axis (brick cell u is t = u + 1): its
+            // offset in cells from the brick centre, t - (extent + 1) / 2
+            const float hx = 0.5f * (float)(ex + 1), hy = 0.5f * (float)(ey + 1), hz = 0.5f * (float)(ez + 1);
             // tile cells 2 lane and 2 lane + 1: first slot and particles, then
             // their bases (exclusive prefix over the tile)
             int js[2] = {0, 0}, nk[2] = {0, 0};
@@ -414,14 +440,14 @@ __global__ void __launch_bounds__(LJ_BRICK_THREADS, 5) k_force_tile_f32(BoxDev b
             s_ts[2 * lane + 1] = js[1];
             s_tn[2 * lane] = nk[0];
             s_tn[2 * lane + 1] = nk[1];
-            if (lane == 31) s_tot = incl;
+            const bool tiled = __shfl_sync(FULL, incl, 31) <= T;
             __syncwarp();
             // brick cells (lane < 8): first slot and particle prefix
             int n8 = 0;
             if (lane < nbc) {
                 const int u = lane & sx, v = (lane >> sx) & sy, w = lane >> (sx + sy);
                 const int t = (u + 1) + tx * (v + 1) + txy * (w + 1);
-                s_cs[lane] = s_ts[t];
+                s_cs[buf][lane] = s_ts[t];
                 n8 = s_tn[t];
             }
             int inc8 = n8;
@@ -430,67 +456,97 @@ __global__ void __launch_bounds__(LJ_BRICK_THREADS, 5) k_force_tile_f32(BoxDev b
                 const int t = __shfl_up_sync(FULL, inc8, o);
                 if (lane >= o) inc8 += t;
             }
-            if (lane < 8) s_pc[lane + 1] = inc8;   // lanes past the brick's cells add nothing
-            if (lane == 0) s_pc[0] = 0;
-        }
-        __syncthreads();   // tile cell table complete
-        const bool tiled = s_tot <= T;   // block-uniform
-        const int npb = s_pc[8];
-        if (tiled) {
-            // a row of the tile (tile cells along x at one y, z) is one run of
-            // tile elements; a warp stages whole rows, up to 128 elements of
-            // a row in flight at once
-            const int nrow = (ey + 2) * (ez + 2);
-            for (int rr = warp; rr < nrow; rr += kBrickWarps) {   // warp-uniform
-                const int t0 = rr * tx;
-                const int rb = s_tb[t0], re = s_tb[t0 + tx - 1] + s_tn[t0 + tx - 1];
-                const float ay = (float)(rr % (ey + 2)) - hy, az = (float)(rr / (ey + 2)) - hz;   // exact
-                for (int e0 = rb; e0 < re; e0 += 128) {
-                    float4 v[4];
-                    int at[4];
+            if (lane < 8) s_pc[buf][lane + 1] = inc8;   // lanes past the brick's cells add nothing
+            const int npb = __shfl_sync(FULL, inc8, 7);
+            if (lane == 0) {
+                s_pc[buf][0] = 0;
+                s_nb[buf] = npb;
+                s_tiled[buf] = tiled ? 1 : 0;
+            }
+            if (tiled) {
+                float* const P = s_dyn + buf * NPL * (T + 1);
+                const uint32_t Xb = X0 + (uint32_t)(buf * BUF);
+                // rows of the tile (tile cells along x at one y, z), 4 elements
+                // per lane in flight
+                const int nrow = (ey + 2) * (ez + 2);
+                for (int rr = 0; rr < nrow; ++rr) {
+                    const int t0 = rr * tx;
+                    const int rb = s_tb[t0], re = s_tb[t0 + tx - 1] + s_tn[t0 + tx - 1];
+                    const float ay = (float)(rr % (ey + 2)) - hy, az = (float)(rr / (ey + 2)) - hz;   // exact
+                    for (int f0 = rb; f0 < re; f0 += 128) {
+                        float4 v[4];
+                        int at[4];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int e = e0 + 32 * u + lane;
-                        int a = 0;   // the tile cell of element e along the row
+                        for (int u = 0; u < 4; ++u) {
+                            const int e = f0 + 32 * u + lane;
+                            int a = 0;   // the tile cell of element e along the row
 #pragma unroll
-                        for (int c = 1; c < 4; ++c) a += (c < tx && s_tb[t0 + c] <= e) ? 1 : 0;
-                        at[u] = a;
-                        v[u] = e < re ? posq[s_ts[t0 + a] + (e - s_tb[t0 + a])] : make_float4(0.f, 0.f, 0.f, 0.f);
-                    }
+                            for (int c = 1; c < 4; ++c) a += (c < tx && s_tb[t0 + c] <= e) ? 1 : 0;
+                            at[u] = a;
+                            v[u] = e < re ? posq[s_ts[t0 + a] + (e - s_tb[t0 + a])] : make_float4(0.f, 0.f, 0.f, 0.f);
+                        }
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int e = e0 + 32 * u + lane;
-                        if (e < re) {
-                            s_t[0][e] = fmaf((float)at[u] - hx, ell.x, v[u].x);
-                            s_t[1][e] = fmaf(ay, ell.y, v[u].y);
-                            s_t[2][e] = fmaf(az, ell.z, v[u].z);
-                            if (!MONO) s_t[NPL - 1][e] = v[u].w;   // type bits
+                        for (int u = 0; u < 4; ++u) {
+                            const int e = f0 + 32 * u + lane;
+                            if (e < re) {
+                                P[e] = fmaf((float)at[u] - hx, ell.x, v[u].x);
+                                P[(T + 1) + e] = fmaf(ay, ell.y, v[u].y);
+                                P[2 * (T + 1) + e] = fmaf(az, ell.z, v[u].z);
+                                if (!MONO) P[(NPL - 1) * (T + 1) + e] = v[u].w;   // type bits
+                            }
                         }
                     }
                 }
+                // address tables: brick cell cl, stencil cell k
+                for (int t = lane; t < nbc * 27; t += 32) {
+                    const int cl = t / 27, kk = t - 27 * cl;
+                    const int u = cl & sx, v = (cl >> sx) & sy, w = cl >> (sx + sy);
+                    const uint32_t dxd = kk % 3, dyd = (kk / 3) % 3, dzd = kk / 9;
+                    const int tc = (u + (int)dxd) + tx * (v + (int)dyd) + txy * (w + (int)dzd);
+                    // (entry << 2) = 4 j + (dx digit << 28) + (dy digit << 30) mod 2^32
+                    s_D[buf][cl][(dzd << 4) | (dyd << 2) | dxd] =
+                        Xb + 4u * (uint32_t)(s_tb[tc] - s_ts[tc]) - (dxd << 28) - (dyd << 30);
+                }
             }
-            // address tables: brick cell cl, stencil cell k
-            for (int t = threadIdx.x; t < nbc * 27; t += blockDim.x) {
-                const int cl = t / 27, k = t - 27 * cl;
-                const int u = cl & sx, v = (cl >> sx) & sy, w = cl >> (sx + sy);
-                const uint32_t dxd = k % 3, dyd = (k / 3) % 3, dzd = k / 9;
-                const int tc = (u + (int)dxd) + tx * (v + (int)dyd) + txy * (w + (int)dzd);
-                // (entry << 2) = 4 j + (dx digit << 28) + (dy digit << 30) mod 2^32
-                s_D[cl][(dzd << 4) | (dyd << 2) | dxd] =
-                    X0 + 4u * (uint32_t)(s_tb[tc] - s_ts[tc]) - (dxd << 28) - (dyd << 30);
-            }
+            mbar_arrive1(&s_full[buf]);   // every producer lane: its stores precede the arrival
         }
-        __syncthreads();   // tile and address tables complete
+        return;
+    }
+
+    // ---------------- consumers ----------------
+    const int grp = threadIdx.x / LJ_TPP, l4 = threadIdx.x % LJ_TPP;
+    const int K = b.K;
+    const float4 mlj = b.c1;
+    const float mrc2 = b.rc2_1, mesh = b.esh_1;
+    const unsigned sent_ent = entry_make(13, b.np);
+    int k = 0;
+    for (int bi = blockIdx.x; bi < b.nbrick; bi += gridDim.x, ++k) {
+        const int buf = k & 1;
+        if (!mbar_wait(&s_full[buf], (k >> 1) & 1)) {
+            if (lane == 0) atomicOr(&b.err[0], LJ_ERRBIT_TIMEOUT);
+            return;
+        }
+        const int4 B = b.brick[bi];
+        const RepDev& R = b.rep[B.x];
+        const int ex = min(R.br[0], R.nc[0] - B.y), ey = min(R.br[1], R.nc[1] - B.z),
+                  ez = min(R.br[2], R.nc[2] - B.w);
+        const int nbc = ex * ey * ez, sx = ex - 1, sy = ey - 1;
+        const float3 ell = make_float3(R.ellf[0], R.ellf[1], R.ellf[2]);
+        const float hx = 0.5f * (float)(ex + 1), hy = 0.5f * (float)(ey + 1), hz = 0.5f * (float)(ez + 1);
+        const bool tiled = s_tiled[buf] != 0;
+        const int npb = s_nb[buf];
+        const uint32_t SENT = X0 + (uint32_t)(buf * BUF) + 4u * (uint32_t)T;
         float e_acc = 0.f, w_acc = 0.f;   // this thread's energy and virial over the brick
         for (int ib = 0; ib < npb; ib += kBrickPass) {
             if (ib + (32 / LJ_TPP) * warp >= npb) break;   // warp-uniform: none of its particles here or later
             const int slot = ib + grp;
             const bool act = slot < npb;
             // its brick cell: the last cl < nbc with s_pc[cl] <= slot (prefix non-decreasing)
-            int cl = (4 < nbc && s_pc[4] <= slot) ? 4 : 0;
-            cl += (cl + 2 < nbc && s_pc[cl + 2] <= slot) ? 2 : 0;
-            cl += (cl + 1 < nbc && s_pc[cl + 1] <= slot) ? 1 : 0;
-            const int p = act ? s_cs[cl] + (slot - s_pc[cl]) : 0;   // no load for an idle group
+            const int* pc = s_pc[buf];
+            int cl = (4 < nbc && pc[4] <= slot) ? 4 : 0;
+            cl += (cl + 2 < nbc && pc[cl + 2] <= slot) ? 2 : 0;
+            cl += (cl + 1 < nbc && pc[cl + 1] <= slot) ? 1 : 0;
+            const int p = act ? s_cs[buf][cl] + (slot - pc[cl]) : 0;   // no load for an idle group
             const float4 pi = act ? posq[p] : make_float4(0.f, 0.f, 0.f, 0.f);
             const uint4* L = reinterpret_cast<const uint4*>(b.nbr + (size_t)K * p) + l4;
             const uint4 z4 = make_uint4(0u, 0u, 0u, 0u);
@@ -510,7 +566,7 @@ __global__ void __launch_bounds__(LJ_BRICK_THREADS, 5) k_force_tile_f32(BoxDev b
                 const float px = fmaf((float)(u + 1) - hx, ell.x, pi.x), py = fmaf((float)(v + 1) - hy, ell.y, pi.y),
                             pz = fmaf((float)(w + 1) - hz, ell.z, pi.z);
                 const float2 nx = make_float2(-px, -px), ny = make_float2(-py, -py), nz = make_float2(-pz, -pz);
-                const uint32_t* D = s_D[cl];
+                const uint32_t* D = s_D[buf][cl];
                 for (int blk = 0; blk + 1 < nblk; ++blk) {
                     const uint4 nx2 = blk + 2 < nblk ? __ldcs(L + (blk + 2) * LJ_TPP) : z4;   // two ahead
                     tile_pair2<MONO, ENERGY, PL>(tile_addr(cur.x, D), tile_addr(cur.y, D), nx, ny, nz, ti, nt, s_lj,
@@ -535,8 +591,8 @@ __global__ void __launch_bounds__(LJ_BRICK_THREADS, 5) k_force_tile_f32(BoxDev b
                     const uint4 nx2 = blk + 2 < nblk ? __ldcs(L + (blk + 2) * LJ_TPP) : z4;
                     uint32_t q[4] = {cur.x, cur.y, cur.z, cur.w};
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const unsigned ek = (!last || lim > k) ? q[k] : sent_ent;
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const unsigned ek = (!last || lim > kk) ? q[kk] : sent_ent;
                         const float4 pj = __ldg(posq + (ek & LJ_IDX_MASK));
                         pair_f32<MONO, ENERGY>(ek, pj, pi, ti, ell, s_lj, s_rc2, s_esh, nt, mlj, mrc2, mesh, fx, fy,
                                                fz, e, vir);
@@ -577,7 +633,7 @@ __global__ void __launch_bounds__(LJ_BRICK_THREADS, 5) k_force_tile_f32(BoxDev b
                 reinterpret_cast<float4*>(b.part_f)[(size_t)bi * kBrickWarps + warp] =
                     make_float4(0.5f * de.x, 0.5f * de.y, 0.5f * dw.x, 0.5f * dw.y);
         }
-        __syncthreads();   // the tile is free for the next brick
+        mbar_arrive1(&s_empty[buf]);   // every consumer thread: its reads of the buffer precede this
     }
 }
 
@@ -1034,6 +1090,23 @@ __global__ void __launch_bounds__(LJ_THERMO_THREADS) k_thermo(BoxDev b, double* 
 
 }  // namespace
 
+// The tiled force kernel's dynamic shared memory (two buffers) is above the
+// default 48 KB: raise the limit once per process.
+static cudaError_t tile_kernel_attrs()
+{
+    static cudaError_t done = cudaErrorNotReady;
+    if (done == cudaErrorNotReady) {
+        cudaError_t e = cudaSuccess;
+        const int dm = (int)(2 * tile_buf_bytes(true)), dx = (int)(2 * tile_buf_bytes(false));
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_force_tile_f32<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, dm);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_force_tile_f32<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, dm);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_force_tile_f32<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, dx);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_force_tile_f32<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, dx);
+        done = e;
+    }
+    return done;
+}
+
 cudaError_t launch_force(const BoxDev& b, int energy, Launch l)
 {
     if (b.all_pairs) {
@@ -1053,12 +1126,16 @@ cudaError_t launch_force(const BoxDev& b, int energy, Launch l)
         if (energy) k_force_f64<true><<<l.grid, LJ_F64_THREADS, 0, l.s>>>(b);
         else k_force_f64<false><<<l.grid, LJ_F64_THREADS, 0, l.s>>>(b);
     } else if (b.force_tiles) {
+        cudaError_t e = tile_kernel_attrs();
+        if (e != cudaSuccess) return e;
+        const int th = LJ_BRICK_THREADS + 32;
+        const size_t dm = 2 * tile_buf_bytes(true), dx = 2 * tile_buf_bytes(false);
         if (b.nt == 1) {
-            if (energy) k_force_tile_f32<true, true><<<l.grid, LJ_BRICK_THREADS, 0, l.s>>>(b);
-            else k_force_tile_f32<true, false><<<l.grid, LJ_BRICK_THREADS, 0, l.s>>>(b);
+            if (energy) k_force_tile_f32<true, true><<<l.grid, th, dm, l.s>>>(b);
+            else k_force_tile_f32<true, false><<<l.grid, th, dm, l.s>>>(b);
         } else {
-            if (energy) k_force_tile_f32<false, true><<<l.grid, LJ_BRICK_THREADS, 0, l.s>>>(b);
-            else k_force_tile_f32<false, false><<<l.grid, LJ_BRICK_THREADS, 0, l.s>>>(b);
+            if (energy) k_force_tile_f32<false, true><<<l.grid, th, dx, l.s>>>(b);
+            else k_force_tile_f32<false, false><<<l.grid, th, dx, l.s>>>(b);
         }
     } else if (b.nt == 1 && b.nrep == 1) {
         if (energy) k_force_f32<true, true, true><<<l.grid, LJ_FORCE_THREADS, 0, l.s>>>(b);
@@ -1078,15 +1155,16 @@ int force_tile_blocks_per_sm(int mono)
 {
     static int occ[2] = {0, 0};
     int& o = occ[mono ? 1 : 0];
-    if (o == 0) {
+    if (o == 0 && tile_kernel_attrs() == cudaSuccess) {
         int v = 0;
-        cudaError_t e = mono ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_force_tile_f32<true, true>,
-                                                                             LJ_BRICK_THREADS, 0)
-                             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_force_tile_f32<false, true>,
-                                                                             LJ_BRICK_THREADS, 0);
-        o = (e == cudaSuccess && v > 0) ? v : 4;
+        const int th = LJ_BRICK_THREADS + 32;
+        cudaError_t e = mono ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_force_tile_f32<true, true>, th,
+                                                                             2 * tile_buf_bytes(true))
+                             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_force_tile_f32<false, true>, th,
+                                                                             2 * tile_buf_bytes(false));
+        o = (e == cudaSuccess && v > 0) ? v : 2;
     }
-    return o;
+    return o > 0 ? o : 2;
 }
 
 cudaError_t launch_thermo(const BoxDev& b, double* out, int with_kin, Launch l)
