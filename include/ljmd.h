@@ -300,11 +300,10 @@ md_status md_get_layout(md_box* b, double* cell_scale, int32_t* order);
  *   MD_LIST_LANES  one warp per cell, one lane per particle of the cell; the
  *                  warp stages each candidate once (dropping those beyond
  *                  the list radius of the cell's box) and every lane tests
- *                  it against its own particle; rows are staged in shared
- *                  memory as 16-bit codes (K + 8 per lane, K the capacity)
- *   MD_LIST_AUTO   (default) MD_LIST_LANES where a block's rows fit in
- *                  96 KB of shared memory (K <= 376), else MD_LIST_QUADS
- * MD_LIST_LANES also falls back to MD_LIST_QUADS when the rows do not fit.
+ *                  it against its own particle; each lane's row is buffered
+ *                  in shared memory as 16-bit codes (48 per lane) and
+ *                  written out in 16-entry blocks
+ *   MD_LIST_AUTO   (default) MD_LIST_LANES
  * The setting takes effect at the next list build. */
 enum { MD_LIST_AUTO = 0, MD_LIST_QUADS = 1, MD_LIST_LANES = 2 };
 md_status md_set_list_kernel(md_box* b, int32_t kind);

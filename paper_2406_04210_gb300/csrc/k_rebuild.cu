@@ -796,6 +796,11 @@ __global__ void __launch_bounds__(LJ_LIST_THREADS, 3) k_nlist(BoxDev b)
 // ---------------------------------------------------------------------------
 constexpr int kLaneWarps = LJ_LANE_THREADS / 32;
 constexpr int kRing = 64;   // staged candidates per warp: < 32 waiting + one chunk
+// Codes a lane holds in shared memory: fewer than 16 not yet written out plus
+// one batch of 32.  Full 16-code blocks go out to the list before a batch
+// that could overflow the buffer, so the rows' shared memory does not grow
+// with the capacity K.
+constexpr int kLaneRow = 48;
 
 // r^2 of the pair (i, candidate q = o_j + shift) from n = -o_i.
 __device__ __forceinline__ float lane_r2(const float2 nxy, float nz, const float4& q)
@@ -806,12 +811,12 @@ __device__ __forceinline__ float lane_r2(const float2 nxy, float nz, const float
     return fmaf(dz, dz, s.x + s.y);
 }
 
-__global__ void __launch_bounds__(LJ_LANE_THREADS, 6) k_nlist_lanes(BoxDev b)
+__global__ void __launch_bounds__(LJ_LANE_THREADS, 8) k_nlist_lanes(BoxDev b)
 {
     if (!box_needs_rebuild(b)) return;
-    // rows, slot-major per warp: code e of lane l at [e][l] (the 32 lanes'
-    // stores of one step fall in distinct banks whatever their counts)
-    extern __shared__ __align__(16) uint16_t s_rows[];   // per warp: (K + 8) x 32 codes
+    // row buffers, slot-major per warp: code e of lane l at [e][l] (the 32
+    // lanes' stores of one step fall in distinct banks whatever their counts)
+    extern __shared__ __align__(16) uint16_t s_rows[];   // per warp: kLaneRow x 32 codes
     __shared__ __align__(16) float s_cx[kLaneWarps][kRing];   // staged candidates: o_j + shift(k),
     __shared__ __align__(16) float s_cy[kLaneWarps][kRing];   // one array per component (pairs of
     __shared__ __align__(16) float s_cz[kLaneWarps][kRing];   // candidates load as one 8-byte word)
@@ -826,8 +831,7 @@ __global__ void __launch_bounds__(LJ_LANE_THREADS, 6) k_nlist_lanes(BoxDev b)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const int K = b.K;
-    uint16_t* const row = s_rows + (size_t)warp * (K + 8) * 32 + lane;   // slot e at row[32 e]
-    // codes past the capacity are counted, written at slot K
+    uint16_t* const row = s_rows + (size_t)warp * kLaneRow * 32 + lane;   // slot e at row[32 e]
     float* const rx = s_cx[warp];
     float* const ry = s_cy[warp];
     float* const rz = s_cz[warp];
@@ -880,15 +884,43 @@ __global__ void __launch_bounds__(LJ_LANE_THREADS, 6) k_nlist_lanes(BoxDev b)
             const float2 nxy = make_float2(-pi.x, -pi.y);
             const float nz = -pi.z;
             const uint32_t self = (13u << LJ_TILE_BITS) | (uint32_t)(ib + lane);   // the particle itself
-            int cnt = 0;                   // codes appended (slots filled, up to K)
+            int cnt = 0;                   // codes in the row buffer
+            int flushed = 0;               // list entries already written out (a multiple of 16)
             unsigned head = 0, tail = 0;   // ring positions (free-running; head stays a multiple of 32)
+            uint4* const dst = reinterpret_cast<uint4*>(b.nbr + (size_t)K * i);   // the particle's row
+            const uint32_t* const base = s_base[warp];
+            // full 16-code blocks out to the list (the entry of cell k's first
+            // slot + index), the rest to the buffer's front; entries past the
+            // capacity are counted, not written
+            auto flush = [&]() {
+                const int nbk = act ? (cnt >> 4) : 0;
+                for (int q = 0; q < nbk; ++q) {
+                    if (flushed + 16 * (q + 1) <= K) {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            uint32_t o[4];
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                const uint32_t h = row[32 * (16 * q + 4 * e + u)];
+                                o[u] = base[h >> LJ_TILE_BITS] + (h & LJ_TILE_MASK);
+                            }
+                            dst[(flushed >> 2) + 4 * q + e] = make_uint4(o[0], o[1], o[2], o[3]);
+                        }
+                    }
+                }
+                const int rest = cnt - 16 * nbk;
+                for (int q = 0; q < rest; ++q) row[32 * q] = row[32 * (16 * nbk + q)];
+                flushed += 16 * nbk;
+                cnt = rest;
+                __syncwarp();
+            };
             // test the staged candidates [head, head + cnt) against the lane's
             // particle and append the hits
             auto batch = [&](int nb) {
                 const int c0 = cnt;
                 const int h0 = (int)(head & (kRing - 1));
                 float m = 0.f;   // largest accepted r^2 of the batch
-                if (nb == 32 && __reduce_min_sync(0xffffffffu, K - cnt) >= 32) {
+                if (nb == 32) {   // the buffer has room for 32 more (flushed before the batch)
                     // branch-free, two candidates per step with FP32-pair
                     // arithmetic: every candidate's code is written to the
                     // next free slot (32-bit shared address), which advances
@@ -922,7 +954,7 @@ __global__ void __launch_bounds__(LJ_LANE_THREADS, 6) k_nlist_lanes(BoxDev b)
                         const float r2 = lane_r2(nxy, nz, q);
                         const uint32_t code = rc[h0 + u];
                         if (r2 < hi2 && code != self) {
-                            row[32 * min(cnt, K)] = (uint16_t)code;
+                            row[32 * cnt] = (uint16_t)code;
                             ++cnt;
                             m = fmaxf(m, r2);
                         }
@@ -931,7 +963,7 @@ __global__ void __launch_bounds__(LJ_LANE_THREADS, 6) k_nlist_lanes(BoxDev b)
                 // FP64 decision of the batch's accepted pairs near rl (rare)
                 if (__any_sync(0xffffffffu, m >= lo2) && m >= lo2) {
                     int w = c0;
-                    const int e = min(cnt, K);
+                    const int e = cnt;
                     for (int q = c0; q < e; ++q) {
                         const uint32_t code = row[32 * q];
                         const int k = (int)(code >> LJ_TILE_BITS);
@@ -941,7 +973,7 @@ __global__ void __launch_bounds__(LJ_LANE_THREADS, 6) k_nlist_lanes(BoxDev b)
                         const float4 qj = make_float4(pj.x + sh.x, pj.y + sh.y, pj.z + sh.z, 0.f);
                         if (lane_r2(nxy, nz, qj) < lo2 || exact_within(b, R, i, j)) row[32 * w++] = (uint16_t)code;
                     }
-                    cnt = w + (cnt - e);   // codes past the capacity stay counted
+                    cnt = w;
                 }
                 head += 32u;
             };
@@ -979,17 +1011,21 @@ __global__ void __launch_bounds__(LJ_LANE_THREADS, 6) k_nlist_lanes(BoxDev b)
                 }
                 tail += __popc(bal);
                 __syncwarp();
-                if (tail - head >= 32) batch(32);
+                if (tail - head >= 32) {
+                    if (__any_sync(0xffffffffu, cnt > kLaneRow - 32)) flush();
+                    batch(32);
+                }
                 __syncwarp();
             }
-            if (tail > head) batch((int)(tail - head));
+            if (tail > head) {
+                if (__any_sync(0xffffffffu, cnt > kLaneRow - 32)) flush();
+                batch((int)(tail - head));
+            }
             __syncwarp();
-            const int c = cnt;
+            const int c = flushed + cnt;
             if (act) {
-                // codes -> list entries (entry of cell k's first slot + index), 4 at a time
-                const int cst = min(c, K);
-                uint4* const dst = reinterpret_cast<uint4*>(b.nbr + (size_t)K * i);
-                const uint32_t* const base = s_base[warp];
+                // the buffer's codes -> list entries, 4 at a time, up to the capacity
+                const int cst = min(cnt, K - flushed);
                 for (int e = 0; 4 * e < cst; ++e) {   // rows end inside a block: masked by the count
                     uint32_t o[4];
 #pragma unroll
@@ -997,7 +1033,7 @@ __global__ void __launch_bounds__(LJ_LANE_THREADS, 6) k_nlist_lanes(BoxDev b)
                         const uint32_t h = row[32 * (4 * e + u)];
                         o[u] = base[h >> LJ_TILE_BITS] + (h & LJ_TILE_MASK);
                     }
-                    dst[e] = make_uint4(o[0], o[1], o[2], o[3]);
+                    dst[(flushed >> 2) + e] = make_uint4(o[0], o[1], o[2], o[3]);
                 }
                 b.nbr_count[i] = c;
                 if (c > K) {
@@ -1078,9 +1114,9 @@ cudaError_t launch_nlist(const BoxDev& b, Launch l)
     return cudaGetLastError();
 }
 
-// Shared memory of k_nlist_lanes for capacity K: K + 8 16-bit code slots
-// per lane (slot K takes the codes past the capacity).
-size_t nlist_lanes_smem(int K) { return (size_t)LJ_LANE_THREADS * (size_t)(K + 8) * 2u; }
+// Shared memory of k_nlist_lanes (any capacity K): kLaneRow 16-bit code
+// slots per lane.
+size_t nlist_lanes_smem(int) { return (size_t)LJ_LANE_THREADS * (size_t)kLaneRow * 2u; }
 
 cudaError_t launch_list_work(const BoxDev& b, cudaStream_t s)
 {

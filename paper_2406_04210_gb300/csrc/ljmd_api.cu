@@ -283,12 +283,11 @@ Launch llist(md_box* b)
     return Launch{std::max(1, std::min(b->d.nseg, b->nsm * per_sm)), LJ_LIST_THREADS, b->stream};
 }
 
-// The lane-per-particle list kernel runs where its rows (K + 4 entries per
-// lane) fit in 96 KB of shared memory per block, unless the quad kernel is
-// asked for.
+// The lane-per-particle list kernel runs unless the quad kernel is asked for
+// (its shared memory does not depend on the capacity).
 bool lanes_list(md_box* b)
 {
-    return b->list_kernel != MD_LIST_QUADS && nlist_lanes_smem(b->d.K) <= 96u * 1024u;
+    return b->list_kernel != MD_LIST_QUADS;
 }
 
 cudaError_t launch_list(md_box* b, cudaStream_t s)
