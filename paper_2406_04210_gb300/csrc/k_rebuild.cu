@@ -818,8 +818,8 @@ __global__ void __launch_bounds__(LJ_LANE_THREADS, 8) k_nlist_lanes(BoxDev b)
     // lanes' stores of one step fall in distinct banks whatever their counts)
     extern __shared__ __align__(16) uint16_t s_rows[];   // per warp: kLaneRow x 32 codes
     __shared__ __align__(16) float s_cx[kLaneWarps][kRing];   // staged candidates: o_j + shift(k),
-    __shared__ __align__(16) float s_cy[kLaneWarps][kRing];   // one array per component (pairs of
-    __shared__ __align__(16) float s_cz[kLaneWarps][kRing];   // candidates load as one 8-byte word)
+    __shared__ __align__(16) float s_cy[kLaneWarps][kRing];   // one array per component (four
+    __shared__ __align__(16) float s_cz[kLaneWarps][kRing];   // candidates load as one 16-byte word)
     __shared__ __align__(16) uint32_t s_cc[kLaneWarps][kRing];   // and their codes
     __shared__ int2 s_rng[kLaneWarps][27];                // neighbour cell k: (first slot, end slot)
     __shared__ float4 s_sh[kLaneWarps][27];               // shift(k) = (dx, dy, dz) * cell edge
@@ -928,22 +928,28 @@ __global__ void __launch_bounds__(LJ_LANE_THREADS, 8) k_nlist_lanes(BoxDev b)
                     uint32_t wa = (uint32_t)__cvta_generic_to_shared(row + 32 * cnt);
                     const float2 px = make_float2(nxy.x, nxy.x), py = make_float2(nxy.y, nxy.y),
                                  pz = make_float2(nz, nz);
-#pragma unroll 4
-                    for (int u = 0; u < 32; u += 2) {
-                        const float2 qx = *reinterpret_cast<const float2*>(rx + h0 + u);
-                        const float2 qy = *reinterpret_cast<const float2*>(ry + h0 + u);
-                        const float2 qz = *reinterpret_cast<const float2*>(rz + h0 + u);
-                        const uint2 cc = *reinterpret_cast<const uint2*>(rc + h0 + u);
+                    // four candidates per step: one 16-byte broadcast load per
+                    // component and for the codes
+                    auto step2 = [&](float2 qx, float2 qy, float2 qz, uint32_t c0, uint32_t c1) {
                         const float2 dx = __fadd2_rn(qx, px), dy = __fadd2_rn(qy, py), dz = __fadd2_rn(qz, pz);
                         const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
-                        const bool h1 = (r2.x < hi2) & (cc.x != self);
-                        asm volatile("st.shared.u16 [%0], %1;" ::"r"(wa), "h"((unsigned short)cc.x));
+                        const bool h1 = (r2.x < hi2) & (c0 != self);
+                        asm volatile("st.shared.u16 [%0], %1;" ::"r"(wa), "h"((unsigned short)c0));
                         wa += h1 ? 64u : 0u;
                         m = fmaxf(m, h1 ? r2.x : 0.f);
-                        const bool h2 = (r2.y < hi2) & (cc.y != self);
-                        asm volatile("st.shared.u16 [%0], %1;" ::"r"(wa), "h"((unsigned short)cc.y));
+                        const bool h2 = (r2.y < hi2) & (c1 != self);
+                        asm volatile("st.shared.u16 [%0], %1;" ::"r"(wa), "h"((unsigned short)c1));
                         wa += h2 ? 64u : 0u;
                         m = fmaxf(m, h2 ? r2.y : 0.f);
+                    };
+#pragma unroll 2
+                    for (int u = 0; u < 32; u += 4) {
+                        const float4 qx = *reinterpret_cast<const float4*>(rx + h0 + u);
+                        const float4 qy = *reinterpret_cast<const float4*>(ry + h0 + u);
+                        const float4 qz = *reinterpret_cast<const float4*>(rz + h0 + u);
+                        const uint4 cc = *reinterpret_cast<const uint4*>(rc + h0 + u);
+                        step2(make_float2(qx.x, qx.y), make_float2(qy.x, qy.y), make_float2(qz.x, qz.y), cc.x, cc.y);
+                        step2(make_float2(qx.z, qx.w), make_float2(qy.z, qy.w), make_float2(qz.z, qz.w), cc.z, cc.w);
                     }
                     asm volatile("" ::: "memory");   // the stores above stay above
                     __syncwarp();                      // and are seen by the reads below
