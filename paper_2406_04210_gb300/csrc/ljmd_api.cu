@@ -293,7 +293,7 @@ bool lanes_list(md_box* b)
 cudaError_t launch_list(md_box* b, cudaStream_t s)
 {
     if (lanes_list(b)) {
-        const int per_sm = b->list_per_sm > 0 ? b->list_per_sm : 4;
+        const int per_sm = b->list_per_sm > 0 ? b->list_per_sm : 8;   // resident blocks (64 registers, 19.5 KB)
         const int warps = LJ_LANE_THREADS / 32;
         return launch_nlist_lanes(
             b->d, Launch{std::max(1, std::min((b->d.ncell + warps - 1) / warps, b->nsm * per_sm)), LJ_LANE_THREADS, s});
