@@ -76,6 +76,31 @@ def test_lj4000_ten_steps(ljmd, kind):
 
 
 @pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("n", [4000, 3472])
+def test_ten_steps_without_energies(ljmd, kind, n):
+    # steps without per-step energies run the kernels' force-only variants;
+    # the monatomic fluid and the binary mixture, against the oracle's run
+    if n == 4000:
+        s = inputs.lj4000()
+    else:
+        s = inputs.binary_random_system(n=n, seed=17)
+        lj = _lj(s)
+        s.pos, _, _ = oracle.fire(s.box, s.pos, lj, s.type, maxit=300, ftol=1e-2)
+        s.vel = np.random.default_rng(3).normal(0.0, np.sqrt(0.7), size=s.pos.shape)
+        s.vel -= s.vel.mean(axis=0)
+    b = ljmd.from_system(s, "mixed_ds")
+    b.force_kernel = kind
+    b.integrate(s.dt, 10, thermo=False)
+    pos, vel, img = b.get_state()
+    types = None if n == 4000 else s.type
+    r = oracle.run(s.box, s.pos, s.vel, _lj(s), s.skin, s.dt, 10, types)
+    d = pos - r["pos"]
+    d -= s.box * np.rint(d / s.box)
+    assert np.abs(d).max() <= 1e-4
+    assert np.abs(vel - r["vel"]).max() <= 1e-4 * np.sqrt(np.mean(s.vel ** 2))
+
+
+@pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("n", [3000, 3472])
 def test_binary_mixture(ljmd, kind, n):
     # density 1.2: n = 3000 gives 4 cells of 3.39 per edge, so a brick's
