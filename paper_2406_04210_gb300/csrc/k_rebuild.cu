@@ -61,15 +61,6 @@ __device__ __forceinline__ void copy_acc(const BoxDev& b, double* dst, const dou
     }
 }
 
-__device__ __forceinline__ double load_off(const BoxDev& b, int c, int p)
-{
-    if (b.prec == 0) {
-        const float* s = reinterpret_cast<const float*>(b.off);
-        return (double)s[c * b.np + p] + (double)s[3 * b.np + c * b.np + p];
-    }
-    return b.off[c * b.np + p];
-}
-
 // ---------------------------------------------------------------------------
 // k_bin: new cell of every particle of a rebuilding replica, its offset from
 // the new cell's centre (offB, the state's layout), its wrapped FP64 position

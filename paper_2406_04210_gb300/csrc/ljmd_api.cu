@@ -1828,7 +1828,7 @@ md_status md_autotune(md_box* b, int32_t reps, int32_t t[4])
     for (int c : fcand) {
         if (b->d.force_tiles) break;
         b->force_per_sm = c;
-        float ms;
+        float ms = 0.f;
         CKS(time_launches(b, reps, [&]() -> md_status { return enqueue_force(b, 1, nullptr); }, &ms));
         if (ms < best_ft) {
             best_ft = ms;
@@ -1846,7 +1846,7 @@ md_status md_autotune(md_box* b, int32_t reps, int32_t t[4])
         CKS(make_segments(b, false));
         for (int lc : lcand) {
             b->list_per_sm = lc;
-            float ms;
+            float ms = 0.f;
             md_status st = time_launches(b, reps, [&]() -> md_status {
                 CKS(set_all_rebuild(b));
                 return enqueue_rebuild(b, b->fresh_abs ? 1 : 0);
@@ -1897,7 +1897,7 @@ md_status md_autotune(md_box* b, int32_t reps, int32_t t[4])
                 const md_status st = set_layout(b, sc, od);
                 if (st == MD_ERR_CAPACITY) continue;   // its tiles overflow: not a candidate
                 if (st != MD_OK) return st;
-                float ms_f, ms_b;
+                float ms_f = 0.f, ms_b = 0.f;
                 CKS(time_launches(b, reps, [&]() -> md_status { return enqueue_force(b, 1, nullptr); }, &ms_f));
                 CKS(time_launches(b, reps, [&]() -> md_status {
                     CKS(set_all_rebuild(b));
@@ -1933,7 +1933,7 @@ md_status md_autotune(md_box* b, int32_t reps, int32_t t[4])
         int best_gl = b->list_per_sm;
         for (int lc : {3, 4, 6, 8, 12, 16, 24}) {
             b->list_per_sm = lc;
-            float ms;
+            float ms = 0.f;
             CKS(time_launches(b, reps, [&]() -> md_status {
                 CKS(set_all_rebuild(b));
                 return enqueue_rebuild(b, b->fresh_abs ? 1 : 0);
