@@ -316,18 +316,23 @@ md_status md_get_list_kernel(md_box* b, int32_t* kind);
  *   MD_FORCE_CHUNKS  work items of 128 consecutive particles, 4 threads per
  *                    particle, neighbour offsets gathered from global memory
  *                    through L1, the image shift decoded from each entry
- *   MD_FORCE_TILES   work items of up to 2 x 2 x 2 cells ("bricks"): the
- *                    brick's neighbourhood (up to 4 x 4 x 4 cells, at most
- *                    2048 particles) staged in shared memory in the frame of
- *                    the brick's centre, 4 threads per particle, two pairs at
- *                    a time in FP32-pair arithmetic; a brick with a larger
- *                    neighbourhood is evaluated from global memory
+ *   MD_FORCE_TILES   work items of up to 2 x 2 x 2 cells ("bricks"): a
+ *                    producer warp stages the next brick's neighbourhood (up
+ *                    to 4 x 4 x 4 cells, at most 2048 particles) into shared
+ *                    memory in the frame of the brick's centre while eight
+ *                    consumer warps compute the current one, 4 threads per
+ *                    particle, two pairs at a time in FP32-pair arithmetic;
+ *                    a brick with a larger neighbourhood is evaluated from
+ *                    global memory; device waits are bounded (a timeout is
+ *                    reported as MD_ERR_TIMEOUT by the call)
  *   MD_FORCE_AUTO    (default) MD_FORCE_CHUNKS until md_autotune times both
  *                    and sets the faster one
  * On the 4M-particle fluid the chunk kernel is the faster (0.54 against
- * 0.66 ms per launch on GB300).  The FP64 precision and the all-pairs form
- * have kernels of their own and ignore the setting.  md_force_noalloc always uses MD_FORCE_CHUNKS.  Takes
- * effect at the next force evaluation; MD_ERR_ARG for another kind. */
+ * 0.65 ms per launch on GB300).  The FP64 precision and the all-pairs form
+ * have kernels of their own and ignore the setting.  md_force_noalloc always
+ * uses MD_FORCE_CHUNKS.  The setting takes effect at the next force
+ * evaluation (the box's step graphs are re-captured); MD_ERR_ARG for another
+ * kind, and md_get_force_kernel returns MD_ERR_ARG for a null pointer. */
 enum { MD_FORCE_AUTO = 0, MD_FORCE_CHUNKS = 1, MD_FORCE_TILES = 2 };
 md_status md_set_force_kernel(md_box* b, int32_t kind);
 md_status md_get_force_kernel(md_box* b, int32_t* kind);
