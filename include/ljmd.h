@@ -76,8 +76,10 @@ typedef enum {
     MD_PREC_FP64 = 2        /* FP64 pair forces and FP64 integration           */
 } md_precision;
 
-/* Device allocator hook: alloc(bytes, ctx) returns a device pointer of the
- * current device aligned to 256 bytes, or NULL; free(ptr, ctx) releases it.
+/* Device allocator hook (no counterpart in the paper: memory plumbing for
+ * hosts such as PyTorch that pool device memory): alloc(bytes, ctx) returns a
+ * device pointer of the current device aligned to 256 bytes, or NULL;
+ * free(ptr, ctx) releases it.
  * Installed process-wide; boxes created afterwards use it for every device
  * allocation they make (at creation, md_set_lj and list regrowth).  Passing
  * NULL functions restores cudaMalloc/cudaFree.  Not thread-safe against
@@ -86,7 +88,9 @@ typedef void* (*md_alloc_fn)(size_t bytes, void* ctx);
 typedef void (*md_free_fn)(void* ptr, void* ctx);
 md_status md_set_allocator(md_alloc_fn alloc, md_free_fn free_, void* ctx);
 
-/* Create a batch of nrep replicas on the current CUDA device.
+/* Create a batch of nrep replicas on the current CUDA device (Sec. 1 and
+ * Sec. 3: N particles in a periodic box; the replicas are independent
+ * systems of that kind).
  *   n[nrep]        particle count of each replica (>= 0)
  *   box[nrep*3]    edge lengths (Lx, Ly, Lz) of each replica (> 0)
  *   type[sum n]    species id of each particle (0 <= type < ntypes given to
@@ -101,12 +105,18 @@ md_status md_batch_create(md_box** out, int32_t nrep, const int64_t* n,
                           const double* pos, const double* vel,
                           md_precision prec, void* stream);
 
-/* md_batch_create with nrep = 1; box[3] is host memory. */
+/* md_batch_create with nrep = 1; box[3] is host memory.  Both copy the
+ * inputs (the caller keeps ownership of its arrays) and return MD_ERR_ARG
+ * for out == NULL, nrep < 1, a negative n, a non-positive or non-finite
+ * edge, pos == NULL with particles, or more than 2^26 particle slots,
+ * MD_ERR_OOM when the allocator fails and MD_ERR_CUDA when a CUDA call
+ * fails. */
 md_status md_box_create(md_box** out, int64_t n, const double box[3],
                         const int32_t* type, const double* pos,
                         const double* vel, md_precision prec, void* stream);
 
-/* Free all device memory of the box (after its queued work completes). */
+/* Free all device memory of the box (after its queued work completes) and
+ * the box itself; MD_ERR_ARG for NULL. */
 md_status md_box_destroy(md_box* b);
 
 /* Set the truncated LJ pair parameters (host arrays, ntypes x ntypes,
@@ -131,8 +141,9 @@ md_status md_set_lj(md_box* b, int32_t ntypes, const double* eps,
  * distribution at T_bath[r] of its replica (unit mass).  The random numbers
  * are Philox4x32-10 (Salmon et al., SC'11) with key = seed + replica index
  * and counter = (index of the particle inside its replica, step index low,
- * step index high, 0 or 1); the step index counts the steps since this call.  Word 0 decides the collision (below
- * floor(rate dt 2^32)); the three Gaussians come by Box-Muller from words 1,
+ * step index high, 0 or 1); the step index counts the steps since this call.
+ * Word 0 decides the collision (below floor(rate dt 2^32)); the three
+ * Gaussians come by Box-Muller from words 1,
  * 2 and from words 0, 1 of the second counter.  Energies are taken after
  * the collisions.  rate = 0 switches it off (the default: NVE).
  *   T_bath  host, nrep entries (> 0), or NULL with rate = 0
@@ -148,13 +159,21 @@ md_status md_set_thermostat(md_box* b, const double* T_bath, double rate,
 md_status md_neighbour_update(md_box* b, int32_t force_rebuild,
                               int32_t* rebuilt);
 
-/* Pair forces at the current positions (updating lists first if needed).
- *   force_out  nullable, (sum n) x 3 FP64, user order
- *   epot, virial nullable, nrep entries each (E_pot and W per replica) */
+/* Pair forces, potential energy and virial at the current positions (Sec.
+ * 4: the Lennard-Jones pair force; Sec. 5, Truncated Force Performance
+ * Study: truncated forces over the Verlet lists), updating the lists first
+ * if the skin rule asks.
+ *   force_out  nullable, (sum n) x 3 FP64, user order, host or device
+ *   epot, virial nullable, nrep entries each (E_pot and W per replica), host
+ *              or device
+ * Returns MD_ERR_ARG before md_set_lj, MD_ERR_NONFINITE for a non-finite
+ * force, MD_ERR_TIMEOUT if a bounded device wait gave up. */
 md_status md_force(md_box* b, double* force_out, double* epot, double* virial);
 
 /* Advance nsteps velocity-Verlet steps of size dt (Sec. 3, Fig. 1:
- * integrate, force, finalize), rebuilding lists by the skin rule.
+ * integrate, force, finalize; Sec. 4: velocity-Verlet), rebuilding lists by
+ * the skin rule (Sec. 3; Sec. 5: the list update).  The steps run as CUDA
+ * graphs of up to 100 steps each, captured on first use.
  *   ckpt_every  0: plain run.  k > 0: record the run for md_adjoint, storing
  *               the state every k steps (nsteps must be a multiple of k).
  *   thermo_out  nullable, nsteps x nrep x 4 FP64: E_pot, E_kin, W, T after
@@ -217,15 +236,19 @@ md_status md_pair_hist(md_box* b, int32_t nbins, double rhist, double width,
 md_status md_force_noalloc(md_box* b, double* force_out, double* epot,
                            double* virial);
 
-/* Current state in user order: pos in [0, L) FP64, vel FP64, image counts
- * (number of box lengths crossed), each nullable. */
+/* Current state in user order (no counterpart in the paper: state access):
+ * pos in [0, L) FP64, vel FP64, image counts (number of box lengths crossed),
+ * each nullable, host or device, (sum n) x 3. */
 md_status md_get_state(md_box* b, double* pos, double* vel, int32_t* image);
 
-/* Replace positions (wrapped into [0,L)) and, if vel != NULL, velocities;
- * image counts are reset to zero; lists are rebuilt and forces recomputed. */
+/* Replace positions (wrapped into [0,L)) and, if vel != NULL, velocities
+ * (no counterpart in the paper: state access); image counts are reset to
+ * zero; lists are rebuilt and forces recomputed; MD_ERR_ARG for a NULL pos
+ * with particles. */
 md_status md_set_state(md_box* b, const double* pos, const double* vel);
 
-/* Neighbour lists as last built, for inspection: count[sum n] (user order)
+/* Neighbour lists as last built, for inspection (Sec. 3: the Verlet lists;
+ * the call itself has no counterpart in the paper): count[sum n] (user order)
  * and, if nbr != NULL, the user indices of each particle's neighbours in
  * nbr[i*cap ...] (unsorted; entries beyond count are left untouched); pos
  * (nullable) receives the FP64 positions the lists were built from.  Returns
@@ -255,7 +278,8 @@ typedef struct {
 
 md_status md_get_info(md_box* b, md_info* out);
 
-/* Launch and layout tuning, t[4]:
+/* Launch and layout tuning (Sec. 3 and Sec. 5: the paper determines launch
+ * configurations per device; here they are set or timed per box), t[4]:
  *   t[0] blocks per SM of the pair-force kernels  (0 = default: 6, FP64 12)
  *   t[1] blocks per SM of the list build          (0 = default: 6)
  *   t[2] cells per list-build segment, <= 16      (0 = automatic: ~1400
