@@ -53,3 +53,9 @@ def test_bad_arguments_rejected_without_gpu(lib):
     h = ctypes.c_void_p()
     assert lib.md_batch_create(ctypes.byref(h), 0, None, None, None, None, None, 0, None) == 1
     assert lib.md_box_destroy(None) == 1
+    # option setters and getters refuse a missing box
+    k = ctypes.c_int32()
+    for setter in ("md_set_force_kernel", "md_set_list_kernel", "md_set_graph_conditional"):
+        assert getattr(lib, setter)(None, 0) == 1, setter
+    for getter in ("md_get_force_kernel", "md_get_list_kernel", "md_get_graph_conditional"):
+        assert getattr(lib, getter)(None, ctypes.byref(k)) == 1, getter
