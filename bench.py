@@ -169,6 +169,8 @@ def run_reference(args):
     # warm-up and timed steps on one sample sized to finish in ~2-3 minutes
     total = args.steps + args.warmup
     n_target = max(4000, min(4_000_000, 150.0 / (6e-6 * max(total, 1))))
+    if args.ref_n:   # a smaller sample (tests)
+        n_target = args.ref_n
     ncell = max(10, int((n_target / 4) ** (1 / 3)))
     import oracle
     from paper_2406_04210_gb300 import inputs
@@ -644,6 +646,8 @@ def main():
                     help="list-build kernel (md_set_list_kernel)")
     ap.add_argument("--force-kernel", default="auto", choices=["auto", "chunks", "tiles"],
                     help="FP32 list-form force kernel (md_set_force_kernel)")
+    ap.add_argument("--ref-n", type=int, default=0,
+                    help="--impl reference: particles of the oracle's sample (default: sized to ~2-3 minutes)")
     ap.add_argument("--cond-graph", action="store_true",
                     help="list update of each step as a conditional graph node (md_set_graph_conditional; "
                          "fewer launches, ~4.5 us slower per step on GB300)")
