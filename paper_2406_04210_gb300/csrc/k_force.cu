@@ -230,14 +230,14 @@ __global__ void __launch_bounds__(LJ_FORCE_THREADS, SINGLE ? 8 : 6) k_force_f32(
 // ---------------------------------------------------------------------------
 // Tiled FP32 pair force (Sec. 4/5: the same forces, energy and virial as
 // k_force_f32; Sec. 5 finds the force kernel bound by fetching neighbour
-// data, which here comes from shared memory).  A block takes one brick of up
-// to 2 x 2 x 2 cells at a time.  It stages the FP32 offsets of the brick's
-// neighbourhood (its cells and the layer of cells around them, up to 64
-// cells) as x, y and z planes of a shared-memory tile, each moved into the
-// frame of the brick's centre by one FMA (q_j = o_j + a ell, a a multiple
-// of 1/2, one rounding), then the brick's particles walk their list rows,
-// LJ_TPP threads per particle, four entries per thread and 16-entry row
-// block.  An entry (stencil digits of neighbour cell k, slot j) names the
+// data, which here comes from shared memory).  The work items are bricks
+// of up to 2 x 2 x 2 cells.  A producer warp stages the FP32 offsets of a
+// brick's neighbourhood (its cells and the layer of cells around them, up to
+// 64 cells) as x, y and z planes of a shared-memory tile, each moved into
+// the frame of the brick's centre by one FMA (q_j = o_j + a ell, a a
+// multiple of 1/2, one rounding), double-buffered; the consumer warps walk
+// the brick's particles' list rows, LJ_TPP threads per particle, four
+// entries per thread and 16-entry row block.  An entry (stencil digits of neighbour cell k, slot j) names the
 // tile element j - start + base of the tile cell at the particle's cell plus
 // k: its byte address is (entry << 2) plus a table word of the particle's
 // cell indexed by the digits, which also cancels what the shift leaves of
