@@ -53,11 +53,18 @@ __device__ __forceinline__ void pair_f32(unsigned ent, const float4& pj, const f
                                          const float* s_esh, int nt, const float4& mlj, float mrc2,
                                          float mesh, float& fx, float& fy, float& fz, float& e, float& vir)
 {
-    // d = (o_i - o_j) - (dx, dy, dz) * ell, one rounding per component
-    const float dx = fmaf(-entry_unit(ent, 26), ell.x, pi.x - pj.x);
-    const float dy = fmaf(-entry_unit(ent, 28), ell.y, pi.y - pj.y);
+    // d = (o_i - o_j) - (dx, dy, dz) * ell, one rounding per component; the
+    // x and y parts as FP32 pairs (a gathered float4 holds them as a register
+    // pair), computed negated: -d = (o_j - o_i) + (dx, dy) * ell, exactly
+    // the negation of the scalar form
+    const float2 uxy = __fadd2_rn(make_float2(__uint_as_float(0x4B400000u | ((ent >> 26) & 3u)),
+                                              __uint_as_float(0x4B400000u | ((ent >> 28) & 3u))),
+                                  make_float2(-12582913.0f, -12582913.0f));
+    const float2 tq = __fadd2_rn(make_float2(pj.x, pj.y), make_float2(-pi.x, -pi.y));
+    const float2 dq = __ffma2_rn(uxy, make_float2(ell.x, ell.y), tq);
     const float dz = fmaf(-entry_unit(ent, 30), ell.z, pi.z - pj.z);
-    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float2 sq = __fmul2_rn(dq, dq);
+    const float r2 = fmaf(dz, dz, sq.x + sq.y);
     float4 c;
     float rc2, esh;
     if (MONO) {
@@ -76,8 +83,8 @@ __device__ __forceinline__ void pair_f32(unsigned ent, const float4& pj, const f
     float f = r2i * r6i * fmaf(c.x, r6i, -c.y);
     const bool in = r2 < rc2;
     f = in ? f : 0.f;
-    fx = fmaf(f, dx, fx);
-    fy = fmaf(f, dy, fy);
+    fx = fmaf(-f, dq.x, fx);
+    fy = fmaf(-f, dq.y, fy);
     fz = fmaf(f, dz, fz);
     if (ENERGY) {
         const float u = fmaf(r6i, fmaf(c.z, r6i, -c.w), -esh);
