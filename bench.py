@@ -626,7 +626,7 @@ def run_gpu(args):
 #: per force kernel, from an ncu capture of the 256,000-particle fluid (fcc
 #: 40^3 x 4, scaled by the particle count); None when the kernel has changed
 #: since.
-DRAM_BYTES_PER_PARTICLE = {"chunks": 416.5, "tiles": None}
+DRAM_BYTES_PER_PARTICLE = {"chunks": 416.0, "tiles": None}
 FORCE_KERNEL_NAMES = {"chunks": "k_force_f32", "tiles": "k_force_tile_f32"}
 
 
